@@ -1,0 +1,96 @@
+"""Write stored expected values for the full-size workloads into tests/golden/configs.json.
+
+Calls only ``oracle`` (and the seeded generators in ``synth``); nothing here comes
+from the GPU path.  Each entry records the graph fingerprint (so a test can tell a
+generator mismatch from a parity failure), the oracle's count and checksum, the
+wall time and the thread count.  Entries are merged into the file one at a time,
+so a long run can be stopped and resumed.
+
+    python oracle/make_golden.py c1            # seconds
+    python oracle/make_golden.py c2 5 7 9      # minutes to hours
+    python oracle/make_golden.py c3blocks 6 7  # per-block values for the SBM workload
+"""
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import oracle as O  # noqa: E402
+from synth import graphs as G  # noqa: E402
+
+PATH = os.path.join(ROOT, "tests", "golden", "configs.json")
+
+
+def _load():
+    if os.path.exists(PATH):
+        return json.load(open(PATH))
+    return {"note": "written by oracle/make_golden.py from the CPU oracle only; counts are decimal strings"}
+
+
+def _store(key, val):
+    d = _load()
+    d[key] = val
+    tmp = PATH + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, PATH)
+    print(key, val, flush=True)
+
+
+def _graph_entry(name, g):
+    cg = O.CleanGraph.of(g)
+    t = time.time()
+    lvl, rnd, nr = O.truss_peel(cg)
+    tp = time.time() - t
+    tri = O.count(cg, 3)
+    _store(f"{name}/graph", {"fingerprint": g.fingerprint(), "n": g.n, "m": g.m,
+                             "tau": int(lvl.max()) if lvl.size else 0, "rounds": nr,
+                             "triangles": str(tri["count"]), "triangle_checksum": str(tri["checksum"]),
+                             "degeneracy": tri["degeneracy"], "peel_s": round(tp, 2)})
+    return cg
+
+
+def _count_entry(name, cg, k, threads):
+    t = time.time()
+    r = O.count(cg, k, shortcut=True, checksum=True, threads=threads)
+    _store(f"{name}/k{k}", {"count": str(r["count"]), "checksum": str(r["checksum"]),
+                            "wall_s": round(time.time() - t, 2), "threads": threads})
+
+
+def main(argv):
+    what = argv[0]
+    ks = [int(x) for x in argv[1:]]
+    threads = int(os.environ.get("ORACLE_THREADS", O.threads_default()))
+    if what == "c1":
+        g = G.config1()
+        cg = _graph_entry("c1", g)
+        for k in ks or [3, 4]:
+            _count_entry("c1", cg, k, threads)
+    elif what == "c2":
+        g = G.chung_lu()
+        cg = _graph_entry("c2", g)
+        for k in ks or [5, 7, 9]:
+            _count_entry("c2", cg, k, threads)
+    elif what == "c3blocks":
+        g, info = G.sbm_2plex()
+        _store("c3/graph", {"fingerprint": g.fingerprint(), "n": g.n, "m": g.m,
+                            "two_plex_blocks": info["two_plex_blocks"]})
+        blk = info["block_of"]
+        u, v = g.edges()
+        for b in [0, 1] + info["two_plex_blocks"][:2]:
+            keep = (blk[u] == b) & (blk[v] == b)
+            sub = G.from_edges(g.n, u[keep], v[keep])
+            cg = O.CleanGraph.of(sub)
+            for k in ks or [6, 7]:
+                _count_entry(f"c3/block{b}", cg, k, threads)
+    else:
+        raise SystemExit(__doc__)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])

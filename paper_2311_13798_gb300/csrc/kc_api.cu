@@ -1,0 +1,233 @@
+// C ABI of libkclique (declared in include/kclique.h).
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kc_internal.cuh"
+
+static thread_local char g_last_error[512];
+
+void kc_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+extern "C" const char *kclique_last_error(void) { return g_last_error; }
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Early-termination threshold t (Sec. 6.1 "Baselines and Metrics": t = 2 when
+// k <= tau/2, else 3).  The kernels implement the closed forms for t <= 2, so a
+// request for t >= 3 runs with t = 2.
+u32 pick_t(const kc_params *p) {
+    u32 t = (p && p->t_max) ? p->t_max : 2u;
+    return std::min<u32>(t, 2u);
+}
+
+kc_status map_device_status(unsigned st) {
+    if (st & KC_DEV_ERR_OVERFLOW) return KC_ERR_OVERFLOW;
+    if (st & KC_DEV_ERR_WIDTH) return KC_ERR_UNSUPPORTED;
+    if (st & KC_DEV_ERR_TIMEOUT) return KC_ERR_TIMEOUT;
+    if (st) return KC_ERR_CUDA;
+    return KC_OK;
+}
+
+u64 suffix_of(const kc_graph *g, u64 x) { return x > g->tau ? 0ull : g->h_size_suffix[x]; }
+
+kc_status check_width(const kc_graph *g, u32 k) {
+    u64 lo = std::max<u64>(KC_MAX_BRANCH + 1, (u64)k - 2);
+    return suffix_of(g, lo) ? KC_ERR_UNSUPPORTED : KC_OK;
+}
+
+kc_status run_one(const kc_graph *g, u32 k, const kc_params *p, cudaStream_t s, kc_result *r, int list, u32 *d_out,
+                  u64 cap) {
+    if (!g || !r) return KC_ERR_INVALID_ARG;
+    memset(r, 0, sizeof(*r));
+    if (k < 3 || k > KC_MAX_K) return KC_ERR_INVALID_ARG;
+    if (list && cap && !d_out) return KC_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    r->ms_prepare = g->ms_prepare;
+    if (p && p->d_edge_count) KC_CUDA(cudaMemsetAsync(p->d_edge_count, 0, sizeof(u64) * (g->m ? g->m : 1), s));
+    if (p && p->d_edge_checksum) KC_CUDA(cudaMemsetAsync(p->d_edge_checksum, 0, sizeof(u64) * (g->m ? g->m : 1), s));
+    if ((u64)k > (u64)g->tau + 2) {  // omega <= tau + 2: no k-clique
+        KC_CUDA(cudaStreamSynchronize(s));
+        return KC_OK;
+    }
+    kc_status st = check_width(g, k);
+    if (st != KC_OK) return st;
+    kc_query q;
+    q.g = g;
+    q.k = k;
+    q.ticket_begin = 0;
+    q.ticket_end = 0;
+    kc_run_cfg cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.t_max = pick_t(p);
+    cfg.flags = p ? p->flags : 0u;
+    cfg.warps_per_block = p ? p->warps_per_block : 0u;
+    cfg.blocks = p ? p->blocks : 0u;
+    cfg.list = list;
+    cfg.d_out = d_out;
+    cfg.cap = cap;
+    cfg.d_edge_count = p ? p->d_edge_count : nullptr;
+    cfg.d_edge_checksum = p ? p->d_edge_checksum : nullptr;
+    kc_dev_acc acc;
+    memset(&acc, 0, sizeof(acc));
+    float ms = 0.f;
+    st = kc_run_queries(&q, 1, &cfg, s, &acc, &ms);
+    if (st != KC_OK) return st;
+    st = map_device_status(acc.status);
+    if (st != KC_OK) return st;
+    r->count_lo = acc.count_lo;
+    r->count_hi = acc.count_hi;
+    r->checksum = (list || (cfg.flags & KC_CHECKSUM)) ? acc.checksum : 0ull;
+    r->written = list ? std::min<u64>(acc.written, cap) : 0ull;
+    r->edge_branches = acc.branches;
+    r->nodes = acc.nodes;
+    r->et_hits = acc.et_hits;
+    r->ms_count = ms;
+    if (list && acc.written > cap) return KC_TRUNCATED;
+    return KC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kc_status kclique_prepare(const uint32_t *row_ptr, const uint32_t *col, uint32_t n, uint64_t nnz, int on_device,
+                          kc_stream s, kc_graph **out) {
+    if (!out) return KC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!row_ptr || (nnz && !col)) return KC_ERR_INVALID_ARG;
+    return kc_prepare_impl(row_ptr, col, n, nnz, on_device, (cudaStream_t)s, out);
+}
+
+kc_status kclique_count(const kc_graph *g, uint32_t k, const kc_params *p, kc_stream s, kc_result *r) {
+    return run_one(g, k, p, (cudaStream_t)s, r, 0, nullptr, 0);
+}
+
+kc_status kclique_list(const kc_graph *g, uint32_t k, uint32_t *d_out, uint64_t cap, const kc_params *p,
+                       kc_stream s, kc_result *r) {
+    return run_one(g, k, p, (cudaStream_t)s, r, 1, d_out, cap);
+}
+
+kc_status kclique_info(const kc_graph *g, kc_info *info) {
+    if (!g || !info) return KC_ERR_INVALID_ARG;
+    memset(info, 0, sizeof(*info));
+    info->n = g->n;
+    info->m = g->m;
+    info->triangles = g->triangles;
+    info->tau = g->tau;
+    info->max_degree = g->max_degree;
+    info->rounds = g->rounds;
+    info->resident_bytes = g->resident_bytes;
+    return KC_OK;
+}
+
+kc_status kclique_edge_data(const kc_graph *g, uint32_t *eu, uint32_t *ev, uint32_t *level, uint32_t *round,
+                            uint32_t *vset_size, kc_stream sv) {
+    if (!g) return KC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)sv;
+    DeviceGuard dg(g->device);
+    const u64 m = g->m;
+    if (m == 0) return KC_OK;
+    if (eu) KC_CUDA(cudaMemcpyAsync(eu, g->eu, sizeof(u32) * m, cudaMemcpyDeviceToHost, s));
+    if (ev) KC_CUDA(cudaMemcpyAsync(ev, g->ev, sizeof(u32) * m, cudaMemcpyDeviceToHost, s));
+    if (level) KC_CUDA(cudaMemcpyAsync(level, g->level, sizeof(u32) * m, cudaMemcpyDeviceToHost, s));
+    if (round) KC_CUDA(cudaMemcpyAsync(round, g->round, sizeof(u32) * m, cudaMemcpyDeviceToHost, s));
+    if (vset_size) {
+        std::vector<u64> ptr(m + 1);
+        KC_CUDA(cudaMemcpyAsync(ptr.data(), g->vset_ptr, sizeof(u64) * (m + 1), cudaMemcpyDeviceToHost, s));
+        KC_CUDA(cudaStreamSynchronize(s));
+        for (u64 i = 0; i < m; i++) vset_size[i] = (u32)(ptr[i + 1] - ptr[i]);
+    }
+    KC_CUDA(cudaStreamSynchronize(s));
+    return KC_OK;
+}
+
+void kclique_release(kc_graph *g) { kc_free_graph(g); }
+
+const char *kclique_status_string(kc_status st) {
+    switch (st) {
+        case KC_OK: return "ok";
+        case KC_TRUNCATED: return "list buffer full: count and checksum cover all cliques";
+        case KC_ERR_INVALID_ARG: return "invalid argument";
+        case KC_ERR_INVALID_GRAPH: return "invalid graph (row_ptr not monotone, column id >= n, or too many entries)";
+        case KC_ERR_OOM: return "device out of memory";
+        case KC_ERR_CUDA: return "CUDA error";
+        case KC_ERR_TIMEOUT: return "bounded device wait timed out";
+        case KC_ERR_OVERFLOW: return "count reached 2^128";
+        case KC_ERR_UNSUPPORTED: return "sub-branch wider than the supported maximum";
+    }
+    return "unknown status";
+}
+
+kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32_t *ks, uint32_t nq, const kc_params *p,
+                              kc_stream sv, kc_result *results) {
+    if (!graphs || !ks || !results) return KC_ERR_INVALID_ARG;
+    if (p && (p->d_edge_count || p->d_edge_checksum)) return KC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)sv;
+    memset(results, 0, sizeof(kc_result) * nq);
+    std::vector<kc_query> qv;
+    std::vector<u32> idx;
+    int dev = -1;
+    for (u32 i = 0; i < nq; i++) {
+        if (!graphs[i] || ks[i] < 3 || ks[i] > KC_MAX_K) return KC_ERR_INVALID_ARG;
+        if (dev < 0) dev = graphs[i]->device;
+        if (graphs[i]->device != dev) return KC_ERR_INVALID_ARG;
+        results[i].ms_prepare = graphs[i]->ms_prepare;
+        if ((u64)ks[i] > (u64)graphs[i]->tau + 2) continue;
+        kc_status st = check_width(graphs[i], ks[i]);
+        if (st != KC_OK) return st;
+        kc_query q;
+        q.g = graphs[i];
+        q.k = ks[i];
+        q.ticket_begin = 0;
+        q.ticket_end = 0;
+        qv.push_back(q);
+        idx.push_back(i);
+    }
+    if (qv.empty()) return KC_OK;
+    DeviceGuard dg(dev);
+    kc_run_cfg cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.t_max = pick_t(p);
+    cfg.flags = p ? p->flags : 0u;
+    cfg.warps_per_block = p ? p->warps_per_block : 0u;
+    cfg.blocks = p ? p->blocks : 0u;
+    std::vector<kc_dev_acc> acc(qv.size());
+    float ms = 0.f;
+    kc_status st = kc_run_queries(qv.data(), (u32)qv.size(), &cfg, s, acc.data(), &ms);
+    if (st != KC_OK) return st;
+    kc_status worst = KC_OK;
+    for (size_t j = 0; j < qv.size(); j++) {
+        kc_result &r = results[idx[j]];
+        kc_status sj = map_device_status(acc[j].status);
+        if (sj != KC_OK) worst = sj;
+        r.count_lo = acc[j].count_lo;
+        r.count_hi = acc[j].count_hi;
+        r.checksum = (cfg.flags & KC_CHECKSUM) ? acc[j].checksum : 0ull;
+        r.edge_branches = acc[j].branches;
+        r.nodes = acc[j].nodes;
+        r.et_hits = acc[j].et_hits;
+        r.ms_count = ms;
+    }
+    return worst;
+}
+
+}  // extern "C"

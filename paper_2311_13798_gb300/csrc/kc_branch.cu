@@ -1,0 +1,1134 @@
+// Branch engine: the per-edge sub-branches of EBBkC-H (paper Alg. 5 lines 2-6,
+// EBBkC-C_Rec of Alg. 4) with early termination (Sec. 5), on one GB300.
+//
+// Work unit = one top-level edge e (a "ticket"), tickets sorted by |VSet(e)|
+// descending and handed out by an atomic counter to persistent warps.  One warp
+// owns a ticket end to end:
+//   A5  extraction: bitset adjacency of g_e on VSet(e), keeping a pair (w, x) only
+//       if (w, x) is an edge that comes after e in the (round, id) order -- the
+//       suffix-graph edges of Eq. 2;
+//   A6  greedy colouring (first fit in non-increasing local degree order, Sec. 4.3)
+//       and renumbering so that positions run in non-increasing colour; the DAG of
+//       Alg. 4 is implicit (out-neighbours = neighbours at larger positions);
+//   A7  edge branching with an explicit per-depth stack; each batch of up to 32
+//       child edges (u -> v) is evaluated lane-per-child: C' = C & N(u) & N(v) &
+//       {positions > v}; Rule (1) limits u and v to colour prefixes, Rule (2)
+//       counts the distinct colours of C' with one carry-propagating add per word;
+//   A8  leaves l = 1 (|C'|) and l = 2 (edges of g[C']) (Alg. 2);
+//   A9  early termination at every frame with l >= 3: a t-plex test on the minimum
+//       degree, then C(|C|, l) for cliques and the kC2Plex count of Alg. 6 in
+//       closed form, sum_j C(|F|, l-j) C(p, j) 2^j, for 2-plexes;
+//   A10 exact 128-bit accumulation (per-lane partials, warp totals, one atomic
+//       add with carry per warp) and the order-independent checksum;
+//   A11 list emission with warp-aggregated slot reservation.
+// Integer work only (AND, POPC, FFS); no tensor cores.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kc_internal.cuh"
+
+namespace {
+
+constexpr int WARPS_PER_BLOCK_DEFAULT = 4;
+constexpr int BINOM_N = 1025;  // C(n, r) for n < BINOM_N
+constexpr int BINOM_R = 33;    //            and r < BINOM_R
+constexpr int MODE_CHECKSUM = 1;
+constexpr int MODE_LIST = 2;
+
+const u128 SAT128 = ~(u128)0;
+
+struct QDesc {
+    const u32 *row_ptr, *col, *pos_eid, *pos_round, *eu, *ev, *round, *vset, *tickets;
+    const u64 *vset_ptr;
+    u32 k;
+    u32 pad;
+    u64 t0;           // first ticket (index into tickets) of this launch's range
+    u64 nt;           // tickets in range
+    kc_dev_acc *acc;
+    u64 *edge_count;
+    u64 *edge_checksum;
+};
+
+struct Args {
+    const QDesc *qs;
+    const u64 *qstart;  // [nq+1] prefix of nt
+    u32 nq;
+    u32 D;              // depth slots in the shared-memory layout
+    u32 warp_bytes;
+    u32 t_max;
+    u32 flags;
+    u32 pad;
+    unsigned long long *ticket_ctr;
+    u32 *d_out;
+    u64 cap;
+    const u128 *binom;
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ u64 zkey(u64 v) {
+    u64 x = v + 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x = x ^ (x >> 31);
+    return x | 1ull;
+}
+
+__device__ __forceinline__ u128 add_sat(u128 a, u128 b) {
+    u128 s = a + b;
+    return (a == SAT128 || b == SAT128 || s < a) ? SAT128 : s;
+}
+
+__device__ __forceinline__ u128 mul_sat(u128 a, u128 b) {
+    if (a == 0 || b == 0) return 0;
+    if (a == SAT128 || b == SAT128) return SAT128;
+    u64 ah = (u64)(a >> 64), bh = (u64)(b >> 64);
+    if (ah == 0 && bh == 0) {
+        u64 al = (u64)a, bl = (u64)b;
+        return ((u128)__umul64hi(al, bl) << 64) | (u128)(al * bl);
+    }
+    if (ah != 0 && bh != 0) return SAT128;
+    if (a > SAT128 / b) return SAT128;
+    return a * b;
+}
+
+__device__ __forceinline__ u128 binom(const u128 *T, int n, int r) {
+    if (r < 0 || r > n) return 0;
+    if (n >= BINOM_N || r >= BINOM_R) return SAT128;
+    return T[n * BINOM_R + r];
+}
+
+// mask of positions > p inside word w
+__device__ __forceinline__ u32 gt_mask(int p, int w) {
+    int pw = p >> 5;
+    if (w < pw) return 0u;
+    if (w > pw) return 0xFFFFFFFFu;
+    int b = p & 31;
+    return b == 31 ? 0u : (0xFFFFFFFFu << (b + 1));
+}
+
+// mask of positions < lim inside word w
+__device__ __forceinline__ u32 lt_mask(int lim, int w) {
+    int lw = lim >> 5;
+    if (w < lw) return 0xFFFFFFFFu;
+    if (w > lw) return 0u;
+    int b = lim & 31;
+    return b == 0 ? 0u : (0xFFFFFFFFu >> (32 - b));
+}
+
+__device__ __forceinline__ u64 warp_sum_u64(u64 x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ u128 warp_sum_u128(u64 x) {
+    // sum of 32 u64 values without overflow: split into halves
+    u64 lo = x & 0xFFFFFFFFull, hi = x >> 32;
+    lo = warp_sum_u64(lo);
+    hi = warp_sum_u64(hi);
+    return ((u128)hi << 32) + (u128)lo;
+}
+
+// ---------------------------------------------------------------- smem layout
+struct Lay {
+    u32 *A;          // [S][W] adjacency rows (undirected, positions)
+    u32 *C0;         // [W] top frame
+    u32 *vid;        // [S] vertex id per position
+    u64 *z;          // [S] key per position
+    uint16_t *col;   // [S] colour per position
+    uint16_t *aux;   // [S] scratch (degree / order / class index)
+    uint16_t *aux2;  // [S] scratch (positions list)
+    uint16_t *lim;   // [S+2] number of positions with colour >= c
+    u32 *J, *E;      // [W] colour segment masks
+    u32 *V;          // [D][W] generator: remaining v candidates
+    int *cur;        // [D] generator: current u
+    int *nchild;     // [D]
+    int *nextc;      // [D]
+    int *slot;       // [D]
+    u32 *childC;     // [D][32][W]
+    u64 *childP;     // [D][32]
+    u32 *childUV;    // [D][32]
+    u32 *path;       // [2D+4]
+    uint16_t *bu, *bv;  // [32]
+    u32 *tmpW;       // [W]
+    u32 *tmpW2;      // [W]
+};
+
+template <int W>
+__host__ __device__ constexpr u32 align16(u32 x) { return (x + 15u) & ~15u; }
+
+template <int W>
+__host__ __device__ u32 lay_bytes(u32 D) {
+    const u32 S = 32u * W;
+    u32 b = 0;
+    b += align16<W>(4u * S * W);       // A
+    b += align16<W>(4u * W);           // C0
+    b += align16<W>(4u * S);           // vid
+    b += align16<W>(8u * S);           // z
+    b += align16<W>(2u * S);           // col
+    b += align16<W>(2u * S);           // aux
+    b += align16<W>(2u * S);           // aux2
+    b += align16<W>(2u * (S + 2));     // lim
+    b += align16<W>(8u * W);           // J, E
+    b += align16<W>(4u * D * W);       // V
+    b += align16<W>(16u * D);          // cur, nchild, nextc, slot
+    b += align16<W>(4u * D * 32 * W);  // childC
+    b += align16<W>(8u * D * 32);      // childP
+    b += align16<W>(4u * D * 32);      // childUV
+    b += align16<W>(4u * (2 * D + 4)); // path
+    b += align16<W>(2u * 64);          // bu, bv
+    b += align16<W>(8u * W);           // tmpW, tmpW2
+    return b;
+}
+
+template <int W>
+__device__ Lay make_lay(unsigned char *p, u32 D) {
+    const u32 S = 32u * W;
+    Lay L;
+    u32 o = 0;
+    L.A = (u32 *)(p + o); o += align16<W>(4u * S * W);
+    L.C0 = (u32 *)(p + o); o += align16<W>(4u * W);
+    L.vid = (u32 *)(p + o); o += align16<W>(4u * S);
+    L.z = (u64 *)(p + o); o += align16<W>(8u * S);
+    L.col = (uint16_t *)(p + o); o += align16<W>(2u * S);
+    L.aux = (uint16_t *)(p + o); o += align16<W>(2u * S);
+    L.aux2 = (uint16_t *)(p + o); o += align16<W>(2u * S);
+    L.lim = (uint16_t *)(p + o); o += align16<W>(2u * (S + 2));
+    L.J = (u32 *)(p + o); L.E = L.J + W; o += align16<W>(8u * W);
+    L.V = (u32 *)(p + o); o += align16<W>(4u * D * W);
+    L.cur = (int *)(p + o); L.nchild = L.cur + D; L.nextc = L.nchild + D; L.slot = L.nextc + D;
+    o += align16<W>(16u * D);
+    L.childC = (u32 *)(p + o); o += align16<W>(4u * D * 32 * W);
+    L.childP = (u64 *)(p + o); o += align16<W>(8u * D * 32);
+    L.childUV = (u32 *)(p + o); o += align16<W>(4u * D * 32);
+    L.path = (u32 *)(p + o); o += align16<W>(4u * (2 * D + 4));
+    L.bu = (uint16_t *)(p + o); L.bv = L.bu + 32; o += align16<W>(2u * 64);
+    L.tmpW = (u32 *)(p + o); L.tmpW2 = L.tmpW + W; o += align16<W>(8u * W);
+    return L;
+}
+
+// ---------------------------------------------------------------- warp primitives
+template <int W>
+__device__ __forceinline__ int warp_popc(const u32 *X, int lane) {
+    int c = lane < W ? __popc(X[lane]) : 0;
+    return __reduce_add_sync(0xffffffffu, (unsigned)c);
+}
+
+// smallest set bit position >= from, or -1
+template <int W>
+__device__ __forceinline__ int warp_first_from(const u32 *X, int from, int lane) {
+    u32 x = 0;
+    if (lane < W) x = X[lane] & ~lt_mask(from, lane);
+    unsigned bal = __ballot_sync(0xffffffffu, x != 0);
+    if (!bal) return -1;
+    int fl = __ffs(bal) - 1;
+    u32 wv = __shfl_sync(0xffffffffu, x, fl);
+    return fl * 32 + __ffs(wv) - 1;
+}
+
+// permute positions: new position r holds old position ord[r] (ord in L.aux2), rows and columns,
+// plus vid / z / extra u16 array (optional)
+// Returns false (and leaves A partly permuted) if ord is not a permutation.
+template <int W>
+__device__ bool permute(const Lay &L, int s, int lane, uint16_t *extra16) {
+    const uint16_t *ord = L.aux2;
+    // columns, row by row (each row is read fully before it is written)
+    int src[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        int r = 32 * w + lane;
+        src[w] = r < s ? ord[r] : -1;
+    }
+    for (int r = 0; r < s; r++) {
+        u32 *row = L.A + r * W;
+        u32 mine = 0;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            int sp = src[w];
+            bool bit = sp >= 0 && ((row[sp >> 5] >> (sp & 31)) & 1u);
+            u32 bal = __ballot_sync(0xffffffffu, bit);
+            if (lane == w) mine = bal;
+        }
+        __syncwarp();
+        if (lane < W) row[lane] = mine;
+        __syncwarp();
+    }
+    // rows: follow the cycles of ord (visited bits in tmpW2)
+    if (lane < W) L.tmpW2[lane] = 0;
+    __syncwarp();
+    int steps = 0;
+    for (int st = 0; st < s; st++) {
+        bool vis = (L.tmpW2[st >> 5] >> (st & 31)) & 1u;
+        if (vis) continue;
+        u32 keep = lane < W ? L.A[st * W + lane] : 0;
+        int j = st;
+        while (true) {
+            if (++steps > s) return false;  // not a permutation: bounded, reported by the caller
+            int sp = ord[j];
+            if (lane == 0) L.tmpW2[j >> 5] |= 1u << (j & 31);
+            if (sp == st) {
+                __syncwarp();
+                if (lane < W) L.A[j * W + lane] = keep;
+                __syncwarp();
+                break;
+            }
+            u32 t = lane < W ? L.A[sp * W + lane] : 0;
+            __syncwarp();
+            if (lane < W) L.A[j * W + lane] = t;
+            __syncwarp();
+            j = sp;
+        }
+    }
+    // per-position arrays
+    u32 vv[W];
+    u64 zz[W];
+    uint16_t ee[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        int r = 32 * w + lane;
+        if (r < s) {
+            vv[w] = L.vid[ord[r]];
+            zz[w] = L.z[ord[r]];
+            ee[w] = extra16 ? extra16[ord[r]] : 0;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        int r = 32 * w + lane;
+        if (r < s) {
+            L.vid[r] = vv[w];
+            L.z[r] = zz[w];
+            if (extra16) extra16[r] = ee[w];
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+// ---------------------------------------------------------------- A5 extraction
+template <int W>
+__device__ void extract(const Lay &L, const QDesc &q, int s, u32 e, u32 re, int lane) {
+    for (int i = lane; i < s * W; i += 32) L.A[i] = 0;
+    __syncwarp();
+    const u32 vmax = L.vid[s - 1];
+    for (int i = 0; i + 1 < s; i++) {
+        const u32 x = L.vid[i];
+        u32 xb = q.row_ptr[x], xe = q.row_ptr[x + 1];
+        // restrict the row to (x, vmax]
+        {
+            u32 lo = xb, hi = xe;
+            while (lo < hi) { u32 mid = (lo + hi) >> 1; if (q.col[mid] <= x) lo = mid + 1; else hi = mid; }
+            xb = lo;
+            lo = xb; hi = xe;
+            while (lo < hi) { u32 mid = (lo + hi) >> 1; if (q.col[mid] <= vmax) lo = mid + 1; else hi = mid; }
+            xe = lo;
+        }
+        const u32 dx = xe - xb;
+        const int rem = s - 1 - i;
+        if (dx <= 4u * (u32)rem) {
+            for (u32 p = xb + lane; p < xe; p += 32) {
+                u32 y = q.col[p];
+                int lo = i + 1, hi = s;
+                while (lo < hi) { int mid = (lo + hi) >> 1; if (L.vid[mid] < y) lo = mid + 1; else hi = mid; }
+                if (lo < s && L.vid[lo] == y) {
+                    u32 rr = q.pos_round[p], ee = q.pos_eid[p];
+                    if (rr > re || (rr == re && ee > e)) {
+                        int j = lo;
+                        atomicOr(&L.A[i * W + (j >> 5)], 1u << (j & 31));
+                        atomicOr(&L.A[j * W + (i >> 5)], 1u << (i & 31));
+                    }
+                }
+            }
+        } else {
+            for (int j = i + 1 + lane; j < s; j += 32) {
+                u32 y = L.vid[j];
+                u32 lo = xb, hi = xe;
+                while (lo < hi) { u32 mid = (lo + hi) >> 1; if (q.col[mid] < y) lo = mid + 1; else hi = mid; }
+                if (lo < xe && q.col[lo] == y) {
+                    u32 rr = q.pos_round[lo], ee = q.pos_eid[lo];
+                    if (rr > re || (rr == re && ee > e)) {
+                        atomicOr(&L.A[i * W + (j >> 5)], 1u << (j & 31));
+                        atomicOr(&L.A[j * W + (i >> 5)], 1u << (i & 31));
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------- A6 colouring
+// Returns the number of colours.  Afterwards positions run in non-increasing
+// colour; L.col[p] is the colour of position p; L.lim[c] = #positions with colour >= c.
+template <int W>
+__device__ int colour_and_order(const Lay &L, int s, int lane) {  // -1: internal error
+    for (int i = lane; i < 32 * W + 2; i += 32) L.lim[i] = 0;
+    // degrees in g_e
+    for (int i = lane; i < s; i += 32) {
+        int d = 0;
+#pragma unroll
+        for (int w = 0; w < W; w++) d += __popc(L.A[i * W + w]);
+        L.aux[i] = (uint16_t)d;
+    }
+    __syncwarp();
+    // order by (degree desc, position asc)
+    for (int i = lane; i < s; i += 32) {
+        int di = L.aux[i], r = 0;
+        for (int j = 0; j < s; j++) {
+            int dj = L.aux[j];
+            r += (dj > di) || (dj == di && j < i);
+        }
+        L.aux2[r] = (uint16_t)i;
+    }
+    __syncwarp();
+    if (!permute<W>(L, s, lane, nullptr)) return -1;
+    // first-fit colouring in position order, one colour class at a time: class c is
+    // the greedy independent set of the still uncoloured positions (identical to
+    // giving each vertex, in order, the least colour unused by earlier neighbours)
+    u32 R = 0;
+    if (lane < W) R = lt_mask(s, lane);
+    int c = 0;
+    while (__any_sync(0xffffffffu, R != 0)) {
+        c++;
+        u32 S = R;
+        int k = 0;
+        while (true) {
+            unsigned bal = __ballot_sync(0xffffffffu, S != 0);
+            if (!bal) break;
+            int fl = __ffs(bal) - 1;
+            u32 wv = __shfl_sync(0xffffffffu, S, fl);
+            int x = fl * 32 + __ffs(wv) - 1;
+            if (lane == 0) { L.col[x] = (uint16_t)c; L.aux[x] = (uint16_t)k; }
+            k++;
+            if (lane == fl) { R &= ~(1u << (x & 31)); S &= ~(1u << (x & 31)); }
+            if (lane < W) S &= ~L.A[x * W + lane];
+        }
+        if (lane == 0) L.lim[c] = (uint16_t)k;  // class size for now
+    }
+    const int ncol = c;
+    __syncwarp();
+    // class sizes -> lim[c] = #positions with colour >= c (suffix sums)
+    if (lane == 0) {
+        int acc = 0;
+        for (int cc = ncol; cc >= 1; cc--) { acc += L.lim[cc]; L.lim[cc] = (uint16_t)acc; }
+        L.lim[ncol + 1] = 0;
+        L.lim[0] = (uint16_t)s;
+    }
+    __syncwarp();
+    // final position of x: positions of colours > col(x), then index within its class
+    for (int x = lane; x < s; x += 32) {
+        int cx = L.col[x];
+        int np = L.lim[cx + 1] + L.aux[x];
+        L.aux2[np] = (uint16_t)x;
+    }
+    __syncwarp();
+    if (!permute<W>(L, s, lane, L.col)) return -1;
+    // segment masks for Rule (2): E = last position of each colour class
+    if (lane < W) { L.E[lane] = 0; L.J[lane] = lt_mask(s, lane); }
+    __syncwarp();
+    if (lane == 0) {
+        for (int cc = 1; cc <= ncol; cc++) {
+            int last = L.lim[cc] - 1;  // classes of colour >= cc end here
+            L.E[last >> 5] |= 1u << (last & 31);
+        }
+        for (int w = 0; w < W; w++) L.J[w] &= ~L.E[w];
+    }
+    __syncwarp();
+    return ncol;
+}
+
+// number of distinct colours in X (Rule 2), one carry-propagating add per word
+template <int W>
+__device__ __forceinline__ int distinct_colours(const u32 (&X)[W], const u32 *J, const u32 *E) {
+    int d = 0;
+    u32 carry = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        u32 j = J[w];
+        u64 t = (u64)(X[w] & j) + (u64)j + carry;
+        carry = (u32)(t >> 32);
+        d += __popc(((u32)t | X[w]) & E[w]);
+    }
+    return d;
+}
+
+// ---------------------------------------------------------------- listing
+__device__ void write_clique(u32 *out, u64 slot, u32 k, const u32 *ids, int nids) {
+    u32 q[KC_MAX_K];
+    for (int i = 0; i < nids; i++) q[i] = ids[i];
+    for (int i = 1; i < nids; i++) {
+        u32 x = q[i];
+        int j = i - 1;
+        while (j >= 0 && q[j] > x) { q[j + 1] = q[j]; j--; }
+        q[j + 1] = x;
+    }
+    u32 *dst = out + slot * k;
+    for (int i = 0; i < nids; i++) dst[i] = q[i];
+}
+
+// ---------------------------------------------------------------- state
+struct Acc {
+    u64 leaf;       // per lane: leaf counts of the current ticket
+    u64 csum;       // per lane: checksum (mod 2^64)
+    u128 cf;        // warp-uniform: closed-form counts of the current ticket
+    u64 cf_csum;    // warp-uniform: closed-form checksum of the current ticket
+    u64 nodes, et;  // per lane (lane 0 counts)
+    u32 status;
+};
+
+// ---------------------------------------------------------------- A9 early termination
+// Returns true if the frame is closed (pruned by size or counted in closed form).
+template <int W, int MODE>
+__device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l, u64 P, int lane, Acc &acc,
+                                bool et_allowed) {
+    const int cnt = warp_popc<W>(C, lane);
+    if (cnt < l) return true;
+    if (!et_allowed) return false;
+    const int tmax = (int)a.t_max;
+    // positions of C -> aux2
+    {
+        u32 x = lane < W ? C[lane] : 0u;
+        int c = __popc(x);
+        int off = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, off, o);
+            if (lane >= o) off += y;
+        }
+        off -= c;
+        while (x) {
+            int b = __ffs(x) - 1;
+            x &= x - 1;
+            L.aux2[off++] = (uint16_t)(lane * 32 + b);
+        }
+    }
+    __syncwarp();
+    // minimum degree inside C (early exit as soon as some vertex is too sparse)
+    int mind = cnt;
+    for (int base = 0; base < cnt; base += 32) {
+        int i = base + lane;
+        int d = cnt;
+        if (i < cnt) {
+            int x = L.aux2[i];
+            d = 0;
+#pragma unroll
+            for (int w = 0; w < W; w++) d += __popc(L.A[x * W + w] & C[w]);
+            L.aux[i] = (uint16_t)d;
+        }
+        d = __reduce_min_sync(0xffffffffu, (unsigned)d);
+        mind = min(mind, d);
+        if (mind < cnt - tmax) return false;
+    }
+    __syncwarp();
+    const int t = cnt - mind;  // 1: clique, 2: 2-plex
+    u128 add = 0;
+    u64 csum = 0;
+    const bool want_sum = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
+    if (t <= 1) {
+        add = binom(a.binom, cnt, l);
+    } else {
+        // F = universal vertices, p = missing pairs (Sec. 5.1, Alg. 6)
+        int nf = 0;
+        for (int base = 0; base < cnt; base += 32) {
+            int i = base + lane;
+            bool f = i < cnt && L.aux[i] == cnt - 1;
+            nf += __popc(__ballot_sync(0xffffffffu, f));
+        }
+        int p = (cnt - nf) / 2;
+        for (int j = 0; j <= p && j <= l; j++) {
+            u128 term = mul_sat(mul_sat(binom(a.binom, nf, l - j), binom(a.binom, p, j)), (u128)1 << j);
+            add = add_sat(add, term);
+        }
+    }
+    if (want_sum) {
+        // coefficient of x^l in prod (1 + c_i x): c = z_f for universal f, z_a + z_b per missing pair
+        u64 e = lane == 0 ? 1ull : 0ull;
+        for (int i = 0; i < cnt; i++) {
+            int x = L.aux2[i];
+            u64 c;
+            if (t <= 1 || L.aux[i] == cnt - 1) {
+                c = L.z[x];
+            } else {
+                // partner: the one non-neighbour of x inside C
+                u32 nb = 0;
+                if (lane < W) nb = C[lane] & ~L.A[x * W + lane] & ~((lane == (x >> 5)) ? (1u << (x & 31)) : 0u);
+                unsigned bal = __ballot_sync(0xffffffffu, nb != 0);
+                int fl = __ffs(bal) - 1;
+                u32 wv = __shfl_sync(0xffffffffu, nb, fl);
+                int y = fl * 32 + __ffs(wv) - 1;
+                if (y < x) continue;
+                c = L.z[x] + L.z[y];
+            }
+            u64 prev = __shfl_up_sync(0xffffffffu, e, 1);
+            if (lane >= 1 && lane <= l) e += c * prev;
+        }
+        csum = __shfl_sync(0xffffffffu, e, l) * P;
+    }
+    if (add == SAT128) acc.status |= KC_DEV_ERR_OVERFLOW;
+    acc.cf = add_sat(acc.cf, add);
+    acc.cf_csum += csum;
+    acc.et++;
+    return true;
+}
+
+// ---------------------------------------------------------------- kernel
+template <int W, int MODE>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK_DEFAULT)
+branch_kernel(Args a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const Lay L = make_lay<W>(smem + (size_t)wib * a.warp_bytes, a.D);
+    const bool use_rule1 = !(a.flags & KC_NO_RULE1);
+    const bool use_rule2 = !(a.flags & KC_NO_RULE2);
+    const bool use_et = !(a.flags & KC_NO_ET) && a.t_max >= 1;
+    constexpr bool SUM = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
+    constexpr bool LIST = (MODE & MODE_LIST) != 0;
+
+    Acc acc;
+    acc.leaf = 0; acc.csum = 0; acc.cf = 0; acc.cf_csum = 0; acc.nodes = 0; acc.et = 0; acc.status = 0;
+    u64 branches = 0;
+    u128 q_total = 0;     // warp total for the current query (lane 0)
+    u64 q_csum = 0;
+    int cur_q = -1;
+
+    auto flush_query = [&](int qi) {
+        // q_total / q_csum are lane-uniform here
+        if (qi < 0) return;
+        const QDesc &q = a.qs[qi];
+        if (lane == 0) {
+            u64 lo = (u64)q_total, hi = (u64)(q_total >> 64);
+            if (lo | hi) {
+                unsigned long long old = atomicAdd(&q.acc->count_lo, (unsigned long long)lo);
+                unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+                if (hi + carry) atomicAdd(&q.acc->count_hi, (unsigned long long)(hi + carry));
+            }
+            if (SUM) atomicAdd(&q.acc->checksum, (unsigned long long)q_csum);
+            atomicAdd(&q.acc->nodes, (unsigned long long)acc.nodes);
+            atomicAdd(&q.acc->et_hits, (unsigned long long)acc.et);
+            atomicAdd(&q.acc->branches, (unsigned long long)branches);
+            if (acc.status) atomicOr(&q.acc->status, acc.status);
+        }
+        q_total = 0; q_csum = 0; acc.nodes = 0; acc.et = 0; branches = 0; acc.status = 0;
+    };
+
+    while (true) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(a.ticket_ctr, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= a.qstart[a.nq]) break;
+        // find the query of ticket t
+        int lo = 0, hi = (int)a.nq - 1;
+        while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (a.qstart[mid] <= t) lo = mid; else hi = mid - 1; }
+        const int qi = lo;
+        if (qi != cur_q) { flush_query(cur_q); cur_q = qi; }
+        const QDesc &q = a.qs[qi];
+        const u32 k = q.k;
+        const int l0 = (int)k - 2;
+        const u32 e = q.tickets[q.t0 + (t - a.qstart[qi])];
+        const u64 vb = q.vset_ptr[e];
+        const int s = (int)(q.vset_ptr[e + 1] - vb);
+        if (s < l0) continue;
+        if (s > 32 * W) { acc.status |= KC_DEV_ERR_WIDTH; continue; }
+        branches++;
+        const u32 eu = q.eu[e], ev = q.ev[e];
+        const u64 P0 = SUM ? zkey(eu) * zkey(ev) : 0ull;
+        for (int i = lane; i < s; i += 32) {
+            u32 v = q.vset[vb + i];
+            L.vid[i] = v;
+            if (SUM) L.z[i] = zkey(v);
+        }
+        if (lane == 0) { L.path[0] = eu; L.path[1] = ev; }
+        __syncwarp();
+        acc.leaf = 0; acc.csum = 0; acc.cf = 0; acc.cf_csum = 0;
+        const bool full0 = LIST && (*(volatile unsigned long long *)&q.acc->written >= a.cap);
+
+        if (l0 == 1) {
+            acc.leaf += (lane == 0) ? (u64)s : 0ull;
+            if (SUM) {
+                u64 zs = 0;
+                for (int i = lane; i < s; i += 32) zs += L.z[i];
+                acc.csum += P0 * zs;
+            }
+            if (LIST && !full0) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&q.acc->written, (unsigned long long)s);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                for (int i = lane; i < s; i += 32) {
+                    if (base + i < a.cap) {
+                        u32 ids[3] = {eu, ev, L.vid[i]};
+                        write_clique(a.d_out, base + i, k, ids, 3);
+                    }
+                }
+            }
+        } else {
+            extract<W>(L, q, s, e, q.round[e], lane);
+            if (l0 == 2) {
+                // edges of g_e
+                for (int i = lane; i < s; i += 32) {
+                    u32 c = 0;
+                    u64 zs = 0;
+#pragma unroll
+                    for (int w = 0; w < W; w++) {
+                        u32 x = L.A[i * W + w] & gt_mask(i, w);
+                        c += __popc(x);
+                        if (SUM) {
+                            while (x) { int b = __ffs(x) - 1; x &= x - 1; zs += L.z[w * 32 + b]; }
+                        }
+                    }
+                    acc.leaf += c;
+                    if (SUM) acc.csum += P0 * L.z[i] * zs;
+                    if (LIST && !full0 && c) {
+                        unsigned long long base = atomicAdd(&q.acc->written, (unsigned long long)c);
+                        u32 idx = 0;
+                        for (int w = 0; w < W; w++) {
+                            u32 x = L.A[i * W + w] & gt_mask(i, w);
+                            while (x) {
+                                int b = __ffs(x) - 1;
+                                x &= x - 1;
+                                if (base + idx < a.cap) {
+                                    u32 ids[4] = {eu, ev, L.vid[i], L.vid[w * 32 + b]};
+                                    write_clique(a.d_out, base + idx, k, ids, 4);
+                                }
+                                idx++;
+                            }
+                        }
+                    }
+                }
+            } else {
+                if (colour_and_order<W>(L, s, lane) < 0) {
+                    acc.status |= KC_DEV_ERR_BOUNDS;
+                    continue;
+                }
+                // ---------------- A7 DFS over frames
+                if (lane < W) L.C0[lane] = lt_mask(s, lane);
+                if (lane == 0) { L.cur[0] = -1; L.slot[0] = 0; }
+                if (lane < W) L.V[lane] = 0;
+                __syncwarp();
+                int d = 0;
+                int phase = 0;  // 0 start frame, 1 generate, 2 descend into children, 3 frame done
+                bool full = full0;
+                while (true) {
+                    const int l = l0 - 2 * d;
+                    const u32 *C = d == 0 ? L.C0 : L.childC + ((size_t)(d * 32 + L.slot[d])) * W;
+                    const u64 P = SUM ? (d == 0 ? P0 : L.childP[d * 32 + L.slot[d]]) : 0ull;
+                    if (phase == 0) {
+                        if (lane == 0) acc.nodes++;
+                        if (LIST) full = *(volatile unsigned long long *)&q.acc->written >= a.cap;
+                        const bool closed = early_terminate<W, MODE>(L, a, C, l, P, lane, acc, use_et && (!LIST || full));
+                        if (closed) { phase = 3; continue; }
+                        if (lane == 0) L.cur[d] = -1;
+                        if (lane < W) L.V[d * W + lane] = 0;
+                        __syncwarp();
+                        phase = 1;
+                        continue;
+                    }
+                    if (phase == 1) {
+                        // fill a batch of up to 32 child edges (u, v)
+                        const int limu = use_rule1 ? (int)L.lim[min(l, 32 * W + 1)] : s;
+                        const int limv = use_rule1 ? (int)L.lim[min(l - 1, 32 * W + 1)] : s;
+                        int nb = 0;
+                        u32 *V = L.V + d * W;
+                        int u = L.cur[d];
+                        while (nb < 32) {
+                            u32 vw = lane < W ? V[lane] : 0u;
+                            int c = __popc(vw);
+                            int tot = __reduce_add_sync(0xffffffffu, (unsigned)c);
+                            if (tot == 0) {
+                                if (u == -2) break;  // generator exhausted
+                                // next u in C with position < limu
+                                int nu = warp_first_from<W>(C, u + 1, lane);
+                                if (nu < 0 || nu >= limu) { u = -2; break; }
+                                u = nu;
+                                u32 nv = 0;
+                                if (lane < W)
+                                    nv = L.A[u * W + lane] & C[lane] & gt_mask(u, lane) & lt_mask(limv, lane);
+                                if (lane < W) V[lane] = nv;
+                                __syncwarp();
+                                continue;
+                            }
+                            int off = c;
+                            for (int o = 1; o < 32; o <<= 1) {
+                                int y = __shfl_up_sync(0xffffffffu, off, o);
+                                if (lane >= o) off += y;
+                            }
+                            off -= c;
+                            int room = 32 - nb;
+                            int take = max(0, min(c, room - off));
+                            for (int i = 0; i < take; i++) {
+                                int b = __ffs(vw) - 1;
+                                vw &= vw - 1;
+                                L.bu[nb + off + i] = (uint16_t)u;
+                                L.bv[nb + off + i] = (uint16_t)(lane * 32 + b);
+                            }
+                            if (lane < W) V[lane] = vw;
+                            nb += min(tot, room);
+                            __syncwarp();
+                        }
+                        if (lane == 0) L.cur[d] = u;
+                        __syncwarp();
+                        if (nb == 0) { phase = 3; continue; }
+                        // evaluate the batch, lane per child
+                        const int l2 = l - 2;
+                        const bool has = lane < nb;
+                        const int cu = has ? L.bu[lane] : 0;
+                        const int cv = has ? L.bv[lane] : 0;
+                        u32 cw[W];
+                        int cc = 0;
+#pragma unroll
+                        for (int w = 0; w < W; w++) {
+                            u32 x = has ? (C[w] & L.A[cu * W + w] & L.A[cv * W + w] & gt_mask(cv, w)) : 0u;
+                            cw[w] = x;
+                            cc += __popc(x);
+                        }
+                        const u64 Pc = SUM ? P * L.z[cu] * L.z[cv] : 0ull;
+                        bool push = false;
+                        if (l2 == 1) {
+                            acc.leaf += (u64)cc;
+                            if (SUM && cc) {
+                                u64 zs = 0;
+#pragma unroll
+                                for (int w = 0; w < W; w++) {
+                                    u32 x = cw[w];
+                                    while (x) { int b = __ffs(x) - 1; x &= x - 1; zs += L.z[w * 32 + b]; }
+                                }
+                                acc.csum += Pc * zs;
+                            }
+                            if (LIST && !full) {
+                                unsigned long long base = 0;
+                                int off2 = cc;
+                                for (int o = 1; o < 32; o <<= 1) {
+                                    int y = __shfl_up_sync(0xffffffffu, off2, o);
+                                    if (lane >= o) off2 += y;
+                                }
+                                int tot2 = __shfl_sync(0xffffffffu, off2, 31);
+                                off2 -= cc;
+                                if (lane == 0 && tot2) base = atomicAdd(&q.acc->written, (unsigned long long)tot2);
+                                base = __shfl_sync(0xffffffffu, base, 0);
+                                u32 ids[KC_MAX_K];
+                                int np = 2 * (d + 1);
+                                for (int i = 0; i < np; i++) ids[i] = L.path[i];
+                                ids[np] = L.vid[cu];
+                                ids[np + 1] = L.vid[cv];
+                                int idx = 0;
+#pragma unroll
+                                for (int w = 0; w < W; w++) {
+                                    u32 x = cw[w];
+                                    while (x) {
+                                        int b = __ffs(x) - 1;
+                                        x &= x - 1;
+                                        if (base + off2 + idx < a.cap) {
+                                            ids[np + 2] = L.vid[w * 32 + b];
+                                            write_clique(a.d_out, base + off2 + idx, k, ids, np + 3);
+                                        }
+                                        idx++;
+                                    }
+                                }
+                            }
+                        } else if (l2 == 2) {
+                            if (cc >= 2) {
+                                u64 ec = 0, zs = 0;
+#pragma unroll
+                                for (int w = 0; w < W; w++) {
+                                    u32 x = cw[w];
+                                    while (x) {
+                                        int b = __ffs(x) - 1;
+                                        x &= x - 1;
+                                        const int xp = w * 32 + b;
+                                        u64 zin = 0;
+#pragma unroll
+                                        for (int w2 = 0; w2 < W; w2++) {
+                                            u32 y = L.A[xp * W + w2] & cw[w2] & gt_mask(xp, w2);
+                                            ec += __popc(y);
+                                            if (SUM) {
+                                                while (y) { int b2 = __ffs(y) - 1; y &= y - 1; zin += L.z[w2 * 32 + b2]; }
+                                            }
+                                        }
+                                        if (SUM) zs += L.z[xp] * zin;
+                                    }
+                                }
+                                acc.leaf += ec;
+                                if (SUM) acc.csum += Pc * zs;
+                                if (LIST && !full && ec) {
+                                    unsigned long long base = atomicAdd(&q.acc->written, (unsigned long long)ec);
+                                    u32 ids[KC_MAX_K];
+                                    int np = 2 * (d + 1);
+                                    for (int i = 0; i < np; i++) ids[i] = L.path[i];
+                                    ids[np] = L.vid[cu];
+                                    ids[np + 1] = L.vid[cv];
+                                    u64 idx = 0;
+                                    for (int w = 0; w < W; w++) {
+                                        u32 x = cw[w];
+                                        while (x) {
+                                            int b = __ffs(x) - 1;
+                                            x &= x - 1;
+                                            const int xp = w * 32 + b;
+                                            for (int w2 = 0; w2 < W; w2++) {
+                                                u32 y = L.A[xp * W + w2] & cw[w2] & gt_mask(xp, w2);
+                                                while (y) {
+                                                    int b2 = __ffs(y) - 1;
+                                                    y &= y - 1;
+                                                    if (base + idx < a.cap) {
+                                                        ids[np + 2] = L.vid[xp];
+                                                        ids[np + 3] = L.vid[w2 * 32 + b2];
+                                                        write_clique(a.d_out, base + idx, k, ids, np + 4);
+                                                    }
+                                                    idx++;
+                                                }
+                                            }
+                                        }
+                                    }
+                                }
+                            }
+                        } else {
+                            push = has && cc >= l2 && (!use_rule2 || distinct_colours<W>(cw, L.J, L.E) >= l2);
+                        }
+                        const unsigned pb = __ballot_sync(0xffffffffu, push);
+                        if (pb) {
+                            const int slotc = __popc(pb & ((1u << lane) - 1));
+                            const int dn = d + 1;
+                            if (push) {
+                                u32 *dst = L.childC + ((size_t)(dn * 32 + slotc)) * W;
+#pragma unroll
+                                for (int w = 0; w < W; w++) dst[w] = cw[w];
+                                if (SUM) L.childP[dn * 32 + slotc] = Pc;
+                                L.childUV[dn * 32 + slotc] = (u32)cu | ((u32)cv << 16);
+                            }
+                            if (lane == 0) { L.nchild[dn] = __popc(pb); L.nextc[dn] = 0; }
+                            __syncwarp();
+                            phase = 2;
+                        }
+                        continue;
+                    }
+                    if (phase == 2) {
+                        const int dn = d + 1;
+                        const int nx = L.nextc[dn];
+                        if (nx < L.nchild[dn]) {
+                            if (lane == 0) {
+                                L.nextc[dn] = nx + 1;
+                                L.slot[dn] = nx;
+                                u32 uv = L.childUV[dn * 32 + nx];
+                                L.path[2 * dn] = L.vid[uv & 0xFFFFu];
+                                L.path[2 * dn + 1] = L.vid[uv >> 16];
+                            }
+                            __syncwarp();
+                            d = dn;
+                            phase = 0;
+                        } else {
+                            phase = 1;
+                        }
+                        continue;
+                    }
+                    // phase 3: frame done
+                    if (d == 0) break;
+                    d--;
+                    phase = 2;
+                }
+            }
+        }
+        // ---------------- end of ticket: totals
+        u128 leaf = warp_sum_u128(acc.leaf);
+        u64 cs = SUM ? warp_sum_u64(acc.csum) + acc.cf_csum : 0ull;
+        u128 tot = leaf + acc.cf;
+        if (tot < leaf || acc.cf == SAT128) acc.status |= KC_DEV_ERR_OVERFLOW;
+        u128 nt = q_total + tot;
+        if (nt < q_total) acc.status |= KC_DEV_ERR_OVERFLOW;
+        q_total = nt;
+        q_csum += cs;
+        if (lane == 0) {
+            if (q.edge_count) q.edge_count[e] = (u64)tot;
+            if (q.edge_checksum) q.edge_checksum[e] = cs;
+        }
+    }
+    flush_query(cur_q);
+}
+
+// ---------------------------------------------------------------- binomials
+__global__ void binom_kernel(u128 *T) {
+    int r = threadIdx.x;
+    for (int n = 0; n < BINOM_N; n++) {
+        if (r < BINOM_R) {
+            u128 v;
+            if (r == 0) v = 1;
+            else if (r > n) v = 0;
+            else {
+                u128 a = T[(n - 1) * BINOM_R + r - 1];
+                u128 b = (r <= n - 1) ? T[(n - 1) * BINOM_R + r] : 0;
+                u128 sum = a + b;
+                v = (a == SAT128 || b == SAT128 || sum < a) ? SAT128 : sum;
+            }
+            T[n * BINOM_R + r] = v;
+        }
+        __syncthreads();
+    }
+}
+
+std::vector<u128 *> g_tables;  // per device
+
+template <int W, int MODE>
+kc_status launch_class(const Args &a0, const std::vector<QDesc> &qs, const kc_run_cfg *cfg, cudaStream_t s,
+                       QDesc *d_qs, u64 *d_qstart, unsigned long long *d_ctr) {
+    Args a = a0;
+    u32 D = 1;
+    for (const QDesc &q : qs) {
+        int l0 = (int)q.k - 2;
+        u32 dq = l0 >= 3 ? (u32)((l0 - 3) / 2 + 1) + 1 : 1;
+        D = std::max(D, dq);
+    }
+    a.D = D;
+    a.warp_bytes = lay_bytes<W>(D);
+    std::vector<u64> qstart(qs.size() + 1, 0);
+    for (size_t i = 0; i < qs.size(); i++) qstart[i + 1] = qstart[i] + qs[i].nt;
+    KC_CUDA(cudaMemcpyAsync(d_qs, qs.data(), sizeof(QDesc) * qs.size(), cudaMemcpyHostToDevice, s));
+    KC_CUDA(cudaMemcpyAsync(d_qstart, qstart.data(), sizeof(u64) * qstart.size(), cudaMemcpyHostToDevice, s));
+    KC_CUDA(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), s));
+    a.qs = d_qs;
+    a.qstart = d_qstart;
+    a.nq = (u32)qs.size();
+    a.ticket_ctr = d_ctr;
+    int wpb = WARPS_PER_BLOCK_DEFAULT;
+    size_t smem = (size_t)a.warp_bytes * wpb;
+    int dev = 0;
+    KC_CUDA(cudaGetDevice(&dev));
+    int max_optin = 0, nsm = 0;
+    KC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    KC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    while (smem > (size_t)max_optin && wpb > 1) { wpb--; smem = (size_t)a.warp_bytes * wpb; }
+    if (smem > (size_t)max_optin) return KC_ERR_UNSUPPORTED;
+    KC_CUDA(cudaFuncSetAttribute(branch_kernel<W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, branch_kernel<W, MODE>, 32 * wpb, smem));
+    if (per_sm < 1) per_sm = 1;
+    u64 total = qstart.back();
+    u64 blocks = (u64)nsm * per_sm;
+    if (cfg->blocks) blocks = cfg->blocks;
+    u64 need = kc_div_up(total, (u64)wpb);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    branch_kernel<W, MODE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}
+
+template <int MODE>
+kc_status launch_mode(int W, const Args &a, const std::vector<QDesc> &qs, const kc_run_cfg *cfg, cudaStream_t s,
+                      QDesc *d_qs, u64 *d_qstart, unsigned long long *d_ctr) {
+    switch (W) {
+        case 1: return launch_class<1, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr);
+        case 2: return launch_class<2, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr);
+        case 4: return launch_class<4, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr);
+        case 8: return launch_class<8, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr);
+        case 16: return launch_class<16, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr);
+        case 32: return launch_class<32, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr);
+    }
+    return KC_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+kc_status kc_ensure_tables(cudaStream_t s) {
+    int dev = 0;
+    KC_CUDA(cudaGetDevice(&dev));
+    if ((int)g_tables.size() <= dev) g_tables.resize(dev + 1, nullptr);
+    if (!g_tables[dev]) {
+        u128 *T = nullptr;
+        KC_CUDA(cudaMalloc(&T, sizeof(u128) * BINOM_N * BINOM_R));
+        binom_kernel<<<1, 64, 0, s>>>(T);
+        KC_CUDA(cudaGetLastError());
+        KC_CUDA(cudaStreamSynchronize(s));
+        g_tables[dev] = T;
+    }
+    return KC_OK;
+}
+
+// Run queries: tickets of each query are split into width classes and every class
+// is one persistent launch over the tickets of all queries in that class.
+kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cudaStream_t s, kc_dev_acc *h_acc,
+                         float *ms) {
+    kc_status st = kc_ensure_tables(s);
+    if (st != KC_OK) return st;
+    int dev = 0;
+    KC_CUDA(cudaGetDevice(&dev));
+    kc_dev_acc *d_acc = nullptr;
+    QDesc *d_qs = nullptr;
+    u64 *d_qstart = nullptr;
+    unsigned long long *d_ctr = nullptr;
+    KC_CUDA(cudaMallocAsync(&d_acc, sizeof(kc_dev_acc) * (nq ? nq : 1), s));
+    KC_CUDA(cudaMemsetAsync(d_acc, 0, sizeof(kc_dev_acc) * (nq ? nq : 1), s));
+    KC_CUDA(cudaMallocAsync(&d_qs, sizeof(QDesc) * (nq ? nq : 1), s));
+    KC_CUDA(cudaMallocAsync(&d_qstart, sizeof(u64) * (nq + 1), s));
+    KC_CUDA(cudaMallocAsync(&d_ctr, sizeof(unsigned long long), s));
+    Args a;
+    memset(&a, 0, sizeof(a));
+    a.t_max = cfg->t_max;
+    a.flags = cfg->flags;
+    a.d_out = cfg->d_out;
+    a.cap = cfg->cap;
+    a.binom = g_tables[dev];
+    int mode = cfg->list ? MODE_LIST : ((cfg->flags & KC_CHECKSUM) ? MODE_CHECKSUM : 0);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    if (cfg->d_edge_count)
+        KC_CUDA(cudaMemsetAsync(cfg->d_edge_count, 0, sizeof(u64) * (nq ? qv[0].g->m : 0), s));
+    if (cfg->d_edge_checksum)
+        KC_CUDA(cudaMemsetAsync(cfg->d_edge_checksum, 0, sizeof(u64) * (nq ? qv[0].g->m : 0), s));
+    const int widths[6] = {32, 16, 8, 4, 2, 1};
+    for (int wi = 0; wi < 6 && st == KC_OK; wi++) {
+        const int W = widths[wi];
+        std::vector<QDesc> qs;
+        for (u32 i = 0; i < nq; i++) {
+            const kc_graph *g = qv[i].g;
+            const u32 k = qv[i].k;
+            const u64 tau = g->tau;
+            auto suffix = [&](u64 x) -> u64 { return x > tau ? 0ull : g->h_size_suffix[x]; };
+            u64 s_hi = 32ull * W;
+            u64 s_lo = (W == 1) ? 0ull : 16ull * W + 1;
+            if (s_lo < k - 2) s_lo = k - 2;
+            if (s_lo > s_hi) continue;
+            u64 b = suffix(s_hi + 1), en = suffix(s_lo);
+            if (en <= b) continue;
+            QDesc d;
+            memset(&d, 0, sizeof(d));
+            d.row_ptr = g->row_ptr; d.col = g->col; d.pos_eid = g->pos_eid; d.pos_round = g->pos_round;
+            d.eu = g->eu; d.ev = g->ev; d.round = g->round; d.vset = g->vset; d.tickets = g->tickets;
+            d.vset_ptr = g->vset_ptr;
+            d.k = k;
+            d.t0 = b;
+            d.nt = en - b;
+            d.acc = d_acc + i;
+            d.edge_count = cfg->d_edge_count;
+            d.edge_checksum = cfg->d_edge_checksum;
+            qs.push_back(d);
+        }
+        if (qs.empty()) continue;
+        if (mode == 0) st = launch_mode<0>(W, a, qs, cfg, s, d_qs, d_qstart, d_ctr);
+        else if (mode == MODE_CHECKSUM) st = launch_mode<MODE_CHECKSUM>(W, a, qs, cfg, s, d_qs, d_qstart, d_ctr);
+        else st = launch_mode<MODE_LIST | MODE_CHECKSUM>(W, a, qs, cfg, s, d_qs, d_qstart, d_ctr);
+        // the query table is reused by the next class: wait for this launch to read it
+        if (st == KC_OK) KC_CUDA(cudaStreamSynchronize(s));
+    }
+    cudaEventRecord(e1, s);
+    if (st == KC_OK) KC_CUDA(cudaMemcpyAsync(h_acc, d_acc, sizeof(kc_dev_acc) * nq, cudaMemcpyDeviceToHost, s));
+    cudaStreamSynchronize(s);
+    cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(d_acc, s);
+    cudaFreeAsync(d_qs, s);
+    cudaFreeAsync(d_qstart, s);
+    cudaFreeAsync(d_ctr, s);
+    cudaStreamSynchronize(s);
+    if (st == KC_OK) {
+        cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) {
+            kc_set_last_cuda_error(ce, "branch kernels", __FILE__, __LINE__);
+            return KC_ERR_CUDA;
+        }
+    }
+    return st;
+}

@@ -1,0 +1,106 @@
+// Internal declarations of libkclique (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kclique.h"
+
+typedef unsigned __int128 u128;
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+#define KC_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) {                                        \
+            kc_set_last_cuda_error(_e, #call, __FILE__, __LINE__);      \
+            return (_e == cudaErrorMemoryAllocation) ? KC_ERR_OOM : KC_ERR_CUDA; \
+        }                                                               \
+    } while (0)
+
+void kc_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// device-side status word bits (set by kernels, read by the host)
+#define KC_DEV_ERR_BOUNDS 0x1u
+#define KC_DEV_ERR_OVERFLOW 0x2u
+#define KC_DEV_ERR_WIDTH 0x4u
+#define KC_DEV_ERR_TIMEOUT 0x8u
+#define KC_DEV_ERR_GRAPH 0x10u
+
+// Device-resident prepared graph.
+struct kc_graph {
+    int device;
+    u32 n;
+    u64 m;        // undirected edges
+    u64 nnz;      // 2m
+    u64 triangles;
+    u32 tau;
+    u32 max_degree;
+    u64 rounds;
+    u64 resident_bytes;
+    float ms_prepare;
+    // CSR (symmetric, sorted, deduplicated, loop free)
+    u32 *row_ptr;     // [n+1]
+    u32 *col;         // [2m]
+    u32 *pos_eid;     // [2m] edge id of each CSR slot
+    u32 *pos_round;   // [2m] peel round of each CSR slot's edge
+    // edges
+    u32 *eu, *ev;     // [m] endpoints u < v
+    u32 *level;       // [m] truss level (trussness - 2)
+    u32 *round;       // [m] peel round; edge order = (round, id)
+    // sub-branch vertex sets (Eq. 2), ascending ids
+    u64 *vset_ptr;    // [m+1]
+    u32 *vset;        // [triangles]
+    // tickets: edge ids sorted by |VSet| descending
+    u32 *tickets;     // [m]
+    // host copy: number of edges with |VSet| >= s, for s = 0..tau+1
+    u64 *h_size_suffix; // [tau + 2]
+    // scratch owned by the handle for count/list calls (reused, guarded by the stream order)
+};
+
+// ---- prepare (kc_prepare.cu)
+kc_status kc_prepare_impl(const u32 *row_ptr, const u32 *col, u32 n, u64 nnz, int on_device,
+                          cudaStream_t s, kc_graph **out);
+void kc_free_graph(kc_graph *g);
+
+// ---- branch engine (kc_branch.cu)
+struct kc_query {
+    const kc_graph *g;
+    u32 k;
+    u64 ticket_begin;   // range of g->tickets to run
+    u64 ticket_end;
+};
+
+struct kc_run_cfg {
+    u32 t_max;
+    u32 flags;
+    u32 warps_per_block;
+    u32 blocks;
+    int list;           // 1 = write cliques
+    u32 *d_out;
+    u64 cap;
+    u64 *d_edge_count;
+    u64 *d_edge_checksum;
+};
+
+// Accumulators in device memory (one per query).
+struct kc_dev_acc {
+    unsigned long long count_lo, count_hi;
+    unsigned long long checksum;
+    unsigned long long written;   // rows reserved (may exceed cap)
+    unsigned long long nodes;
+    unsigned long long et_hits;
+    unsigned long long branches;
+    unsigned int status;
+    unsigned int pad;
+};
+
+kc_status kc_run_queries(const kc_query *q, u32 nq, const kc_run_cfg *cfg, cudaStream_t s,
+                         kc_dev_acc *h_acc, float *ms);
+
+// binomial table on the device (saturating u128), built on first use per device
+kc_status kc_ensure_tables(cudaStream_t s);
+
+// ---- small host helpers
+static inline u64 kc_div_up(u64 a, u64 b) { return (a + b - 1) / b; }

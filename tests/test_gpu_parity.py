@@ -1,0 +1,265 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, bit-exact.
+
+Counts, checksums, listings, truss levels and rounds, VSet sizes and per-edge
+sub-branch counts are integers, so every comparison is exact equality.  Graphs
+span several bitset words and ragged tails (sub-branches of 1..300 vertices),
+and the degenerate cases of the method: empty graphs, triangle-free graphs
+(tau = 0), k > tau + 2, complete graphs (ET on the whole sub-branch), exact
+2-plexes, t-plexes, duplicate / self-loop / one-directional input.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import graphs as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+M64 = (1 << 64) - 1
+
+
+def kc():
+    from paper_2311_13798_gb300 import kclique
+    return kclique
+
+
+def dev_csr(g):
+    rp = torch.from_numpy(g.row_ptr.astype(np.int32)).cuda()
+    col = torch.from_numpy(g.col.astype(np.int32)).cuda()
+    return rp, col
+
+
+def prep(g):
+    rp, col = dev_csr(g)
+    return kc().kclique_prepare(rp, col, g.n)
+
+
+GRAPHS = {
+    "gnp60": lambda: G.gnp(60, 0.3, seed=1),
+    "gnp120_dense": lambda: G.gnp(120, 0.6, seed=2),
+    "gnp400": lambda: G.gnp(400, 0.08, seed=3),
+    "k40": lambda: G.complete(40),
+    "k70": lambda: G.complete(70),
+    "turan": lambda: G.complete_multipartite([7, 8, 9, 10, 11, 6]),
+    "two_plex": lambda: G.two_plex(9, 12),
+    "t3plex": lambda: G.t_plex(45, 3, seed=4),
+    "appendix_b": lambda: G.appendix_b(),
+    "kpp": lambda: G.complete_bipartite(12, 12),
+    "chung_lu": lambda: G.chung_lu(n=4000, w_max=400.0, i0=40.0, planted=6, planted_min=12, planted_max=30, seed=5),
+    "sbm": lambda: G.sbm_2plex(blocks=8, block_size=60, p_in=0.85, p_out=0.01, two_plex_blocks=3, seed=6)[0],
+    "wide": lambda: G.gnp(300, 0.75, seed=7),   # sub-branches of ~170 vertices (6 words)
+}
+
+
+# largest k the oracle finishes in seconds on each graph
+KMAX = {"wide": 5, "gnp400": 6}
+
+
+@pytest.fixture(scope="module")
+def cache():
+    return {}
+
+
+def get(cache, name):
+    if name not in cache:
+        g = GRAPHS[name]()
+        cache[name] = (g, O.CleanGraph.of(g), prep(g))
+    return cache[name]
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_prepare_matches_oracle(cache, name):
+    g, cg, h = get(cache, name)
+    info = kc().kclique_info(h)
+    assert info["n"] == g.n and info["m"] == g.m
+    ed = kc().kclique_edge_data(h)
+    assert (ed["eu"] == cg.eu).all() and (ed["ev"] == cg.ev).all()
+    lvl, rnd, nr = O.truss_peel(cg)
+    assert (ed["level"] == lvl).all()
+    assert (ed["round"] == rnd).all()
+    assert info["rounds"] == nr
+    vs = O.vset_sizes(cg, rnd)
+    assert (ed["vset_size"] == vs).all()
+    assert info["triangles"] == int(vs.sum()) == O.count(cg, 3)["count"]
+    assert info["tau"] == (int(lvl.max()) if lvl.size else 0)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_count_and_checksum(cache, name):
+    g, cg, h = get(cache, name)
+    tau = kc().kclique_info(h)["tau"]
+    for k in range(3, KMAX.get(name, 9) + 1):
+        want = O.count(cg, k)
+        got = kc().kclique_count(h, k, flags=kc().KC_CHECKSUM)
+        assert got["count"] == want["count"], (name, k)
+        assert got["checksum"] == want["checksum"], (name, k)
+        if k > tau + 2:
+            assert got["count"] == 0
+
+
+@pytest.mark.parametrize("name", ["gnp120_dense", "k40", "two_plex", "t3plex", "chung_lu", "sbm", "wide"])
+@pytest.mark.parametrize("flags", [0x1, 0x2, 0x8, 0x1 | 0x2 | 0x8])
+def test_ablation_flags_do_not_change_results(cache, name, flags):
+    g, cg, h = get(cache, name)
+    K = kc()
+    for k in range(4, min(KMAX.get(name, 7), 7) + 1):
+        want = O.count(cg, k)
+        got = K.kclique_count(h, k, flags=flags | K.KC_CHECKSUM)
+        assert (got["count"], got["checksum"]) == (want["count"], want["checksum"]), (name, k, flags)
+
+
+@pytest.mark.parametrize("t_max", [1, 2])
+def test_early_termination_thresholds(cache, t_max):
+    for name in ("k70", "two_plex", "t3plex", "sbm"):
+        g, cg, h = get(cache, name)
+        for k in (5, 6, 8):
+            want = O.count(cg, k)
+            got = kc().kclique_count(h, k, t_max=t_max, flags=kc().KC_CHECKSUM)
+            assert (got["count"], got["checksum"]) == (want["count"], want["checksum"])
+
+
+def test_early_termination_fires_on_cliques_and_2plexes(cache):
+    for name in ("k70", "two_plex"):
+        g, cg, h = get(cache, name)
+        got = kc().kclique_count(h, 6)
+        assert got["et_hits"] > 0
+
+
+@pytest.mark.parametrize("name", ["gnp60", "gnp120_dense", "k40", "turan", "two_plex", "t3plex", "appendix_b",
+                                  "chung_lu", "sbm"])
+def test_list_matches_oracle(cache, name):
+    g, cg, h = get(cache, name)
+    for k in (3, 4, 5, 6):
+        want = O.count(cg, k)
+        cap = max(want["count"], 1)
+        if cap > 3_000_000:
+            continue
+        out = torch.full((cap, k), -1, dtype=torch.int32, device="cuda")
+        got = kc().kclique_list(h, k, out)
+        assert not got["truncated"]
+        assert got["count"] == want["count"] and got["written"] == want["count"]
+        assert got["checksum"] == want["checksum"]
+        rows = out[: got["written"]].cpu().numpy().astype(np.int64)
+        if rows.size:
+            assert (np.diff(rows, axis=1) > 0).all()
+        ref = O.list_cliques(cg, k).astype(np.int64)
+        assert sorted(map(tuple, rows.tolist())) == sorted(map(tuple, ref.tolist()))
+
+
+def test_list_truncation_keeps_full_count(cache):
+    g, cg, h = get(cache, "gnp120_dense")
+    k = 5
+    want = O.count(cg, k)
+    cap = want["count"] // 3
+    out = torch.zeros((cap, k), dtype=torch.int32, device="cuda")
+    got = kc().kclique_list(h, k, out)
+    assert got["truncated"] and got["written"] == cap
+    assert got["count"] == want["count"] and got["checksum"] == want["checksum"]
+    rows = set(map(tuple, out.cpu().numpy().astype(np.int64).tolist()))
+    ref = set(map(tuple, O.list_cliques(cg, k).astype(np.int64).tolist()))
+    assert len(rows) == cap and rows <= ref
+
+
+def test_per_edge_counts(cache):
+    for name in ("chung_lu", "sbm", "gnp120_dense"):
+        g, cg, h = get(cache, name)
+        _, rnd, _ = O.truss_peel(cg)
+        m = g.m
+        for k in (4, 6, 7):
+            ec = torch.zeros(m, dtype=torch.int64, device="cuda")
+            es = torch.zeros(m, dtype=torch.int64, device="cuda")
+            got = kc().kclique_count(h, k, edge_count=ec, edge_checksum=es, flags=kc().KC_CHECKSUM)
+            rng = np.random.default_rng(k)
+            sample = np.unique(np.concatenate([rng.choice(m, size=min(m, 150), replace=False),
+                                               np.argsort(-O.vset_sizes(cg, rnd))[:20]]))
+            cnt, cs = O.edge_counts(cg, k, rnd, sample)
+            gc = ec.cpu().numpy().view(np.uint64)
+            gs = es.cpu().numpy().view(np.uint64)
+            assert [int(x) for x in gc[sample]] == cnt
+            assert [int(x) for x in gs[sample]] == cs
+            assert int(gc.astype(object).sum()) == got["count"]
+
+
+def test_host_input_and_dirty_csr():
+    """Host arrays, duplicates, self-loops and one-directional edges are cleaned."""
+    g = G.gnp(150, 0.3, seed=9)
+    u, v = g.edges()
+    rng = np.random.default_rng(0)
+    # keep each edge in one random direction, add duplicates and self loops
+    flip = rng.random(u.size) < 0.5
+    a = np.where(flip, v, u)
+    b = np.where(flip, u, v)
+    dup = rng.choice(u.size, 200)
+    a = np.concatenate([a, a[dup], np.arange(20)])
+    b = np.concatenate([b, b[dup], np.arange(20)])
+    order = np.argsort(a, kind="stable")
+    a, b = a[order], b[order]
+    rp = np.zeros(g.n + 1, dtype=np.uint32)
+    rp[1:] = np.cumsum(np.bincount(a, minlength=g.n))
+    K = kc()
+    h = K.kclique_prepare(rp, b.astype(np.uint32), g.n)
+    assert K.kclique_info(h)["m"] == g.m
+    for k in (3, 4, 5):
+        want = O.count(g, k)
+        got = K.kclique_count(h, k, flags=K.KC_CHECKSUM)
+        assert (got["count"], got["checksum"]) == (want["count"], want["checksum"])
+
+
+def test_empty_and_invalid():
+    K = kc()
+    h = K.kclique_prepare(np.zeros(6, np.uint32), np.zeros(0, np.uint32), 5)
+    assert K.kclique_info(h)["m"] == 0
+    assert K.kclique_count(h, 3)["count"] == 0
+    with pytest.raises(K.KCliqueError):
+        K.kclique_count(h, 2)
+    with pytest.raises(K.KCliqueError):
+        K.kclique_count(h, 33)
+    with pytest.raises(K.KCliqueError):  # column id out of range
+        K.kclique_prepare(np.array([0, 1], np.uint32), np.array([5], np.uint32), 1)
+    with pytest.raises(K.KCliqueError):  # row_ptr not monotone
+        K.kclique_prepare(np.array([0, 2, 1], np.uint32), np.array([1, 0], np.uint32), 2)
+
+
+def test_relabel_invariance():
+    g = G.gnp(200, 0.25, seed=10)
+    perm = G.random_perm(200, 1, 2)
+    h1, h2 = prep(g), prep(G.relabel(g, perm))
+    for k in (4, 5, 6):
+        a = kc().kclique_count(h1, k)["count"]
+        b = kc().kclique_count(h2, k)["count"]
+        assert a == b == O.count(g, k)["count"]
+
+
+def test_batch_matches_single(cache):
+    names = ["gnp60", "k40", "two_plex", "chung_lu", "sbm", "kpp", "appendix_b"]
+    hs, ks, want = [], [], []
+    for i, name in enumerate(names * 2):
+        g, cg, h = get(cache, name)
+        k = 3 + (i % 6)
+        hs.append(h)
+        ks.append(k)
+        want.append(O.count(cg, k))
+    K = kc()
+    res = K.kclique_count_batch(hs, ks, flags=K.KC_CHECKSUM)
+    for r, w in zip(res, want):
+        assert (r["count"], r["checksum"]) == (w["count"], w["checksum"])
+
+
+def test_overflow_is_reported():
+    # K_300: C(300, 30) ~ 1.7e41 > 2^128 closed forms saturate -> KC_ERR_OVERFLOW
+    K = kc()
+    h = prep(G.complete(300))
+    with pytest.raises(K.KCliqueError) as ei:
+        K.kclique_count(h, 32)
+    assert ei.value.status == K.KC_ERR_OVERFLOW
+
+
+def test_large_counts_exceed_64_bits():
+    """K_200 at k = 20: C(200, 20) = 1.6e27 > 2^64, exact in 128 bits."""
+    import math
+    K = kc()
+    h = prep(G.complete(200))
+    got = K.kclique_count(h, 20, flags=K.KC_CHECKSUM)
+    assert got["count"] == math.comb(200, 20)
+    assert got["checksum"] == O.count(G.complete(200), 20)["checksum"]
