@@ -83,6 +83,7 @@ typedef struct {
     uint32_t flags;            /* KC_NO_ET | KC_NO_RULE2 | KC_CHECKSUM | KC_NO_RULE1 */
     uint64_t *d_edge_count;    /* optional device [m]: k-cliques whose first edge is e (mod 2^64) */
     uint64_t *d_edge_checksum; /* optional device [m]: their checksum */
+    uint64_t *d_edge_cycles;   /* optional device [m]: SM clock cycles the warp spent on e's sub-branch */
 } kc_params;
 
 typedef struct {
@@ -92,8 +93,14 @@ typedef struct {
     uint64_t edge_branches;      /* top-level sub-branches run (|VSet(e)| >= k-2) */
     uint64_t nodes;              /* branch frames expanded */
     uint64_t et_hits;            /* frames closed by early termination */
+    uint64_t word_ops;           /* algorithmic bitset lane-ops: 3 per 32-bit word of every
+                                    candidate-set intersection (AND, AND, POPC), 2 per word of
+                                    every degree test (AND, POPC) */
+    uint64_t pair_tests;         /* adjacency tests made while extracting sub-branches */
     float ms_prepare;            /* device time of the prepare call that built the graph */
     float ms_count;              /* device time of this call */
+    float ms_branch;             /* device time of the branch kernels alone */
+    float pad;
 } kc_result;
 
 typedef struct {
@@ -164,6 +171,14 @@ KC_API const char *kclique_last_error(void);
  */
 KC_API kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32_t *ks, uint32_t nq,
                               const kc_params *p, kc_stream s, kc_result *results);
+
+/*
+ * kclique_int_peak -- measurement utility (no counterpart in the paper): the sustained
+ * rate of the branch kernel's inner operation mix, AND + AND + POPC on 32-bit words held
+ * in registers, on the current device, in lane-ops per second (3 per word), with the SM
+ * count.  Used as the denominator of the integer roofline.
+ */
+KC_API kc_status kclique_int_peak(double *lane_ops_per_s, int *sms, kc_stream s);
 
 #ifdef __cplusplus
 }

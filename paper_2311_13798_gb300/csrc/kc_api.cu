@@ -64,6 +64,7 @@ kc_status run_one(const kc_graph *g, u32 k, const kc_params *p, cudaStream_t s, 
     r->ms_prepare = g->ms_prepare;
     if (p && p->d_edge_count) KC_CUDA(cudaMemsetAsync(p->d_edge_count, 0, sizeof(u64) * (g->m ? g->m : 1), s));
     if (p && p->d_edge_checksum) KC_CUDA(cudaMemsetAsync(p->d_edge_checksum, 0, sizeof(u64) * (g->m ? g->m : 1), s));
+    if (p && p->d_edge_cycles) KC_CUDA(cudaMemsetAsync(p->d_edge_cycles, 0, sizeof(u64) * (g->m ? g->m : 1), s));
     if ((u64)k > (u64)g->tau + 2) {  // omega <= tau + 2: no k-clique
         KC_CUDA(cudaStreamSynchronize(s));
         return KC_OK;
@@ -86,10 +87,11 @@ kc_status run_one(const kc_graph *g, u32 k, const kc_params *p, cudaStream_t s, 
     cfg.cap = cap;
     cfg.d_edge_count = p ? p->d_edge_count : nullptr;
     cfg.d_edge_checksum = p ? p->d_edge_checksum : nullptr;
+    cfg.d_edge_cycles = p ? p->d_edge_cycles : nullptr;
     kc_dev_acc acc;
     memset(&acc, 0, sizeof(acc));
-    float ms = 0.f;
-    st = kc_run_queries(&q, 1, &cfg, s, &acc, &ms);
+    float ms = 0.f, msb = 0.f;
+    st = kc_run_queries(&q, 1, &cfg, s, &acc, &ms, &msb);
     if (st != KC_OK) return st;
     st = map_device_status(acc.status);
     if (st != KC_OK) return st;
@@ -100,7 +102,10 @@ kc_status run_one(const kc_graph *g, u32 k, const kc_params *p, cudaStream_t s, 
     r->edge_branches = acc.branches;
     r->nodes = acc.nodes;
     r->et_hits = acc.et_hits;
+    r->word_ops = acc.word_ops;
+    r->pair_tests = acc.pair_tests;
     r->ms_count = ms;
+    r->ms_branch = msb;
     if (list && acc.written > cap) return KC_TRUNCATED;
     return KC_OK;
 }
@@ -180,7 +185,7 @@ const char *kclique_status_string(kc_status st) {
 kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32_t *ks, uint32_t nq, const kc_params *p,
                               kc_stream sv, kc_result *results) {
     if (!graphs || !ks || !results) return KC_ERR_INVALID_ARG;
-    if (p && (p->d_edge_count || p->d_edge_checksum)) return KC_ERR_INVALID_ARG;
+    if (p && (p->d_edge_count || p->d_edge_checksum || p->d_edge_cycles)) return KC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)sv;
     memset(results, 0, sizeof(kc_result) * nq);
     std::vector<kc_query> qv;
@@ -211,8 +216,8 @@ kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32_t *ks,
     cfg.warps_per_block = p ? p->warps_per_block : 0u;
     cfg.blocks = p ? p->blocks : 0u;
     std::vector<kc_dev_acc> acc(qv.size());
-    float ms = 0.f;
-    kc_status st = kc_run_queries(qv.data(), (u32)qv.size(), &cfg, s, acc.data(), &ms);
+    float ms = 0.f, msb = 0.f;
+    kc_status st = kc_run_queries(qv.data(), (u32)qv.size(), &cfg, s, acc.data(), &ms, &msb);
     if (st != KC_OK) return st;
     kc_status worst = KC_OK;
     for (size_t j = 0; j < qv.size(); j++) {
@@ -225,7 +230,10 @@ kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32_t *ks,
         r.edge_branches = acc[j].branches;
         r.nodes = acc[j].nodes;
         r.et_hits = acc[j].et_hits;
+        r.word_ops = acc[j].word_ops;
+        r.pair_tests = acc[j].pair_tests;
         r.ms_count = ms;
+        r.ms_branch = msb;
     }
     return worst;
 }

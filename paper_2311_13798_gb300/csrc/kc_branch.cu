@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <vector>
@@ -51,6 +52,7 @@ struct QDesc {
     kc_dev_acc *acc;
     u64 *edge_count;
     u64 *edge_checksum;
+    u64 *edge_cycles;
 };
 
 struct Args {
@@ -309,9 +311,21 @@ __device__ bool permute(const Lay &L, int s, int lane, uint16_t *extra16) {
     return true;
 }
 
+// ---------------------------------------------------------------- state
+struct Acc {
+    u64 leaf;       // per lane: leaf counts of the current ticket
+    u64 csum;       // per lane: checksum (mod 2^64)
+    u128 cf;        // warp-uniform: closed-form counts of the current ticket
+    u64 cf_csum;    // warp-uniform: closed-form checksum of the current ticket
+    u64 nodes, et;  // per lane (lane 0 counts)
+    u64 ops;        // per lane: algorithmic word-ops (3 per word of an intersection, 2 per degree word)
+    u64 pairs;      // per lane: adjacency tests during extraction
+    u32 status;
+};
+
 // ---------------------------------------------------------------- A5 extraction
 template <int W>
-__device__ void extract(const Lay &L, const QDesc &q, int s, u32 e, u32 re, int lane) {
+__device__ void extract(const Lay &L, const QDesc &q, int s, u32 e, u32 re, int lane, Acc &acc) {
     for (int i = lane; i < s * W; i += 32) L.A[i] = 0;
     __syncwarp();
     const u32 vmax = L.vid[s - 1];
@@ -331,6 +345,7 @@ __device__ void extract(const Lay &L, const QDesc &q, int s, u32 e, u32 re, int 
         const int rem = s - 1 - i;
         if (dx <= 4u * (u32)rem) {
             for (u32 p = xb + lane; p < xe; p += 32) {
+                acc.pairs++;
                 u32 y = q.col[p];
                 int lo = i + 1, hi = s;
                 while (lo < hi) { int mid = (lo + hi) >> 1; if (L.vid[mid] < y) lo = mid + 1; else hi = mid; }
@@ -345,6 +360,7 @@ __device__ void extract(const Lay &L, const QDesc &q, int s, u32 e, u32 re, int 
             }
         } else {
             for (int j = i + 1 + lane; j < s; j += 32) {
+                acc.pairs++;
                 u32 y = L.vid[j];
                 u32 lo = xb, hi = xe;
                 while (lo < hi) { u32 mid = (lo + hi) >> 1; if (q.col[mid] < y) lo = mid + 1; else hi = mid; }
@@ -470,21 +486,12 @@ __device__ void write_clique(u32 *out, u64 slot, u32 k, const u32 *ids, int nids
     for (int i = 0; i < nids; i++) dst[i] = q[i];
 }
 
-// ---------------------------------------------------------------- state
-struct Acc {
-    u64 leaf;       // per lane: leaf counts of the current ticket
-    u64 csum;       // per lane: checksum (mod 2^64)
-    u128 cf;        // warp-uniform: closed-form counts of the current ticket
-    u64 cf_csum;    // warp-uniform: closed-form checksum of the current ticket
-    u64 nodes, et;  // per lane (lane 0 counts)
-    u32 status;
-};
 
 // ---------------------------------------------------------------- A9 early termination
 // Returns true if the frame is closed (pruned by size or counted in closed form).
 template <int W, int MODE>
 __device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l, u64 P, int lane, Acc &acc,
-                                bool et_allowed) {
+                                bool et_allowed, int ws) {
     const int cnt = warp_popc<W>(C, lane);
     if (cnt < l) return true;
     if (!et_allowed) return false;
@@ -517,6 +524,7 @@ __device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l
 #pragma unroll
             for (int w = 0; w < W; w++) d += __popc(L.A[x * W + w] & C[w]);
             L.aux[i] = (uint16_t)d;
+            acc.ops += 2u * (u32)ws;
         }
         d = __reduce_min_sync(0xffffffffu, (unsigned)d);
         mind = min(mind, d);
@@ -590,6 +598,7 @@ branch_kernel(Args a) {
 
     Acc acc;
     acc.leaf = 0; acc.csum = 0; acc.cf = 0; acc.cf_csum = 0; acc.nodes = 0; acc.et = 0; acc.status = 0;
+    acc.ops = 0; acc.pairs = 0;
     u64 branches = 0;
     u128 q_total = 0;     // warp total for the current query (lane 0)
     u64 q_csum = 0;
@@ -599,7 +608,10 @@ branch_kernel(Args a) {
         // q_total / q_csum are lane-uniform here
         if (qi < 0) return;
         const QDesc &q = a.qs[qi];
+        const u64 ops = warp_sum_u64(acc.ops), pairs = warp_sum_u64(acc.pairs);
         if (lane == 0) {
+            atomicAdd(&q.acc->word_ops, (unsigned long long)ops);
+            atomicAdd(&q.acc->pair_tests, (unsigned long long)pairs);
             u64 lo = (u64)q_total, hi = (u64)(q_total >> 64);
             if (lo | hi) {
                 unsigned long long old = atomicAdd(&q.acc->count_lo, (unsigned long long)lo);
@@ -613,6 +625,7 @@ branch_kernel(Args a) {
             if (acc.status) atomicOr(&q.acc->status, acc.status);
         }
         q_total = 0; q_csum = 0; acc.nodes = 0; acc.et = 0; branches = 0; acc.status = 0;
+        acc.ops = 0; acc.pairs = 0;
     };
 
     while (true) {
@@ -629,11 +642,13 @@ branch_kernel(Args a) {
         const u32 k = q.k;
         const int l0 = (int)k - 2;
         const u32 e = q.tickets[q.t0 + (t - a.qstart[qi])];
+        const long long t_start = clock64();
         const u64 vb = q.vset_ptr[e];
         const int s = (int)(q.vset_ptr[e + 1] - vb);
         if (s < l0) continue;
         if (s > 32 * W) { acc.status |= KC_DEV_ERR_WIDTH; continue; }
         branches++;
+        const int Ws = (s + 31) >> 5;  // words a sub-branch of s vertices needs
         const u32 eu = q.eu[e], ev = q.ev[e];
         const u64 P0 = SUM ? zkey(eu) * zkey(ev) : 0ull;
         for (int i = lane; i < s; i += 32) {
@@ -665,7 +680,7 @@ branch_kernel(Args a) {
                 }
             }
         } else {
-            extract<W>(L, q, s, e, q.round[e], lane);
+            extract<W>(L, q, s, e, q.round[e], lane, acc);
             if (l0 == 2) {
                 // edges of g_e
                 for (int i = lane; i < s; i += 32) {
@@ -680,6 +695,7 @@ branch_kernel(Args a) {
                         }
                     }
                     acc.leaf += c;
+                    acc.ops += 2u * (u32)(Ws - (i >> 5));
                     if (SUM) acc.csum += P0 * L.z[i] * zs;
                     if (LIST && !full0 && c) {
                         unsigned long long base = atomicAdd(&q.acc->written, (unsigned long long)c);
@@ -718,7 +734,7 @@ branch_kernel(Args a) {
                     if (phase == 0) {
                         if (lane == 0) acc.nodes++;
                         if (LIST) full = *(volatile unsigned long long *)&q.acc->written >= a.cap;
-                        const bool closed = early_terminate<W, MODE>(L, a, C, l, P, lane, acc, use_et && (!LIST || full));
+                        const bool closed = early_terminate<W, MODE>(L, a, C, l, P, lane, acc, use_et && (!LIST || full), Ws);
                         if (closed) { phase = 3; continue; }
                         if (lane == 0) L.cur[d] = -1;
                         if (lane < W) L.V[d * W + lane] = 0;
@@ -785,6 +801,7 @@ branch_kernel(Args a) {
                             cc += __popc(x);
                         }
                         const u64 Pc = SUM ? P * L.z[cu] * L.z[cv] : 0ull;
+                        if (has) acc.ops += 3u * (u32)(Ws - (cv >> 5));
                         bool push = false;
                         if (l2 == 1) {
                             acc.leaf += (u64)cc;
@@ -838,6 +855,7 @@ branch_kernel(Args a) {
                                         int b = __ffs(x) - 1;
                                         x &= x - 1;
                                         const int xp = w * 32 + b;
+                                        acc.ops += 3u * (u32)(Ws - (xp >> 5));
                                         u64 zin = 0;
 #pragma unroll
                                         for (int w2 = 0; w2 < W; w2++) {
@@ -941,6 +959,7 @@ branch_kernel(Args a) {
         if (lane == 0) {
             if (q.edge_count) q.edge_count[e] = (u64)tot;
             if (q.edge_checksum) q.edge_checksum[e] = cs;
+            if (q.edge_cycles) q.edge_cycles[e] = (u64)(clock64() - t_start);
         }
     }
     flush_query(cur_q);
@@ -1047,7 +1066,7 @@ kc_status kc_ensure_tables(cudaStream_t s) {
 // Run queries: tickets of each query are split into width classes and every class
 // is one persistent launch over the tickets of all queries in that class.
 kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cudaStream_t s, kc_dev_acc *h_acc,
-                         float *ms) {
+                         float *ms, float *ms_branch) {
     kc_status st = kc_ensure_tables(s);
     if (st != KC_OK) return st;
     int dev = 0;
@@ -1072,11 +1091,15 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    *ms_branch = 0.f;
     cudaEventRecord(e0, s);
     if (cfg->d_edge_count)
         KC_CUDA(cudaMemsetAsync(cfg->d_edge_count, 0, sizeof(u64) * (nq ? qv[0].g->m : 0), s));
     if (cfg->d_edge_checksum)
         KC_CUDA(cudaMemsetAsync(cfg->d_edge_checksum, 0, sizeof(u64) * (nq ? qv[0].g->m : 0), s));
+    if (cfg->d_edge_cycles)
+        KC_CUDA(cudaMemsetAsync(cfg->d_edge_cycles, 0, sizeof(u64) * (nq ? qv[0].g->m : 0), s));
+    const bool profile = getenv("KC_PROFILE") != nullptr;
     const int widths[6] = {32, 16, 8, 4, 2, 1};
     for (int wi = 0; wi < 6 && st == KC_OK; wi++) {
         const int W = widths[wi];
@@ -1103,14 +1126,31 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
             d.acc = d_acc + i;
             d.edge_count = cfg->d_edge_count;
             d.edge_checksum = cfg->d_edge_checksum;
+            d.edge_cycles = cfg->d_edge_cycles;
             qs.push_back(d);
         }
         if (qs.empty()) continue;
+        cudaEvent_t b0, b1;
+        cudaEventCreate(&b0);
+        cudaEventCreate(&b1);
+        cudaEventRecord(b0, s);
         if (mode == 0) st = launch_mode<0>(W, a, qs, cfg, s, d_qs, d_qstart, d_ctr);
         else if (mode == MODE_CHECKSUM) st = launch_mode<MODE_CHECKSUM>(W, a, qs, cfg, s, d_qs, d_qstart, d_ctr);
         else st = launch_mode<MODE_LIST | MODE_CHECKSUM>(W, a, qs, cfg, s, d_qs, d_qstart, d_ctr);
+        cudaEventRecord(b1, s);
         // the query table is reused by the next class: wait for this launch to read it
         if (st == KC_OK) KC_CUDA(cudaStreamSynchronize(s));
+        float bm = 0.f;
+        cudaEventElapsedTime(&bm, b0, b1);
+        *ms_branch += bm;
+        if (profile) {
+            u64 nt = 0;
+            for (const QDesc &d : qs) nt += d.nt;
+            fprintf(stderr, "[kclique] class W=%d queries=%zu tickets=%llu mode=%d %.3f ms\n", W, qs.size(),
+                    (unsigned long long)nt, mode, bm);
+        }
+        cudaEventDestroy(b0);
+        cudaEventDestroy(b1);
     }
     cudaEventRecord(e1, s);
     if (st == KC_OK) KC_CUDA(cudaMemcpyAsync(h_acc, d_acc, sizeof(kc_dev_acc) * nq, cudaMemcpyDeviceToHost, s));
@@ -1131,4 +1171,62 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
         }
     }
     return st;
+}
+
+// ---------------------------------------------------------------- integer peak probe
+// Sustained rate of the inner mix of the branch kernel: for every 32-bit word, two ANDs
+// and a POPC (fused by the compiler into LOP3 + POPC + IADD), 8 independent chains per
+// thread.  Counts 3 lane-ops per word, the accounting used for word_ops.
+__global__ void int_peak_kernel(u32 seed, int iters, unsigned long long *sink) {
+    u32 a[8], b[8], c[8];
+    u32 acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        a[i] = seed * (threadIdx.x + 1 + i) ^ blockIdx.x;
+        b[i] = seed + 0x9E3779B9u * (i + 1) + threadIdx.x;
+        c[i] = ~a[i] ^ (b[i] << 7);
+    }
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            u32 x = a[i] & b[i] & c[i];
+            acc += __popc(x);
+            a[i] = b[i];
+            b[i] = c[i];
+            c[i] = x ^ (u32)it;
+        }
+    }
+    if (acc == 0x7FFFFFFFu) atomicAdd(sink, 1ull);  // keeps the loop alive
+}
+
+extern "C" KC_API kc_status kclique_int_peak(double *lane_ops_per_s, int *sms, kc_stream sv) {
+    if (!lane_ops_per_s) return KC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)sv;
+    int dev = 0, nsm = 0;
+    KC_CUDA(cudaGetDevice(&dev));
+    KC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    unsigned long long *sink = nullptr;
+    KC_CUDA(cudaMalloc(&sink, sizeof(unsigned long long)));
+    const int threads = 256, blocks = nsm * 8, iters = 1 << 14;
+    int_peak_kernel<<<blocks, threads, 0, s>>>(12345u, iters / 16, sink);  // warm-up
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 5; rep++) {
+        cudaEventRecord(e0, s);
+        int_peak_kernel<<<blocks, threads, 0, s>>>(12345u + rep, iters, sink);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    KC_CUDA(cudaGetLastError());
+    *lane_ops_per_s = 3.0 * 8.0 * (double)iters * threads * blocks / (best * 1e-3);
+    if (sms) *sms = nsm;
+    return KC_OK;
 }

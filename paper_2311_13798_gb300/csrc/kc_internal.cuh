@@ -82,6 +82,7 @@ struct kc_run_cfg {
     u64 cap;
     u64 *d_edge_count;
     u64 *d_edge_checksum;
+    u64 *d_edge_cycles;
 };
 
 // Accumulators in device memory (one per query).
@@ -92,12 +93,14 @@ struct kc_dev_acc {
     unsigned long long nodes;
     unsigned long long et_hits;
     unsigned long long branches;
+    unsigned long long word_ops;
+    unsigned long long pair_tests;
     unsigned int status;
     unsigned int pad;
 };
 
 kc_status kc_run_queries(const kc_query *q, u32 nq, const kc_run_cfg *cfg, cudaStream_t s,
-                         kc_dev_acc *h_acc, float *ms);
+                         kc_dev_acc *h_acc, float *ms, float *ms_branch);
 
 // binomial table on the device (saturating u128), built on first use per device
 kc_status kc_ensure_tables(cudaStream_t s);

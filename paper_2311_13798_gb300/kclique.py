@@ -36,13 +36,15 @@ KC_NO_RULE1 = 0x8
 
 class KcParams(C.Structure):
     _fields_ = [("t_max", C.c_uint32), ("warps_per_block", C.c_uint32), ("blocks", C.c_uint32),
-                ("flags", C.c_uint32), ("d_edge_count", C.c_void_p), ("d_edge_checksum", C.c_void_p)]
+                ("flags", C.c_uint32), ("d_edge_count", C.c_void_p), ("d_edge_checksum", C.c_void_p),
+                ("d_edge_cycles", C.c_void_p)]
 
 
 class KcResult(C.Structure):
     _fields_ = [("count_lo", C.c_uint64), ("count_hi", C.c_uint64), ("checksum", C.c_uint64),
                 ("written", C.c_uint64), ("edge_branches", C.c_uint64), ("nodes", C.c_uint64),
-                ("et_hits", C.c_uint64), ("ms_prepare", C.c_float), ("ms_count", C.c_float)]
+                ("et_hits", C.c_uint64), ("word_ops", C.c_uint64), ("pair_tests", C.c_uint64),
+                ("ms_prepare", C.c_float), ("ms_count", C.c_float), ("ms_branch", C.c_float), ("pad", C.c_float)]
 
 
 class KcInfo(C.Structure):
@@ -91,6 +93,8 @@ def _load():
             lib.kclique_status_string.argtypes = [C.c_int]
             lib.kclique_last_error.restype = C.c_char_p
             lib.kclique_last_error.argtypes = []
+            lib.kclique_int_peak.restype = C.c_int
+            lib.kclique_int_peak.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int), vp]
             lib.kclique_count_batch.restype = C.c_int
             lib.kclique_count_batch.argtypes = [C.POINTER(vp), C.POINTER(u32), u32, C.POINTER(KcParams), vp,
                                                 C.POINTER(KcResult)]
@@ -170,18 +174,21 @@ def kclique_prepare(row_ptr, col, n: int | None = None, stream=None) -> Graph:
     return Graph(h.value)
 
 
-def _params(t_max=0, flags=0, blocks=0, warps_per_block=0, edge_count=None, edge_checksum=None):
+def _params(t_max=0, flags=0, blocks=0, warps_per_block=0, edge_count=None, edge_checksum=None,
+            edge_cycles=None):
     p = KcParams()
     p.t_max, p.flags, p.blocks, p.warps_per_block = t_max, flags, blocks, warps_per_block
     p.d_edge_count = edge_count.data_ptr() if edge_count is not None else None
     p.d_edge_checksum = edge_checksum.data_ptr() if edge_checksum is not None else None
+    p.d_edge_cycles = edge_cycles.data_ptr() if edge_cycles is not None else None
     return p
 
 
 def _result(r: KcResult, status: int) -> dict:
     return {"count": int(r.count_lo) | (int(r.count_hi) << 64), "checksum": int(r.checksum),
             "written": int(r.written), "edge_branches": int(r.edge_branches), "nodes": int(r.nodes),
-            "et_hits": int(r.et_hits), "ms_prepare": float(r.ms_prepare), "ms_count": float(r.ms_count),
+            "et_hits": int(r.et_hits), "word_ops": int(r.word_ops), "pair_tests": int(r.pair_tests),
+            "ms_prepare": float(r.ms_prepare), "ms_count": float(r.ms_count), "ms_branch": float(r.ms_branch),
             "truncated": status == KC_TRUNCATED, "status": status}
 
 
@@ -238,3 +245,13 @@ def kclique_count_batch(graphs: list[Graph], ks, stream=None, **kw) -> list[dict
     if st != KC_OK:
         raise KCliqueError(st, "kclique_count_batch")
     return [_result(res[i], KC_OK) for i in range(nq)]
+
+
+def kclique_int_peak(stream=None) -> dict:
+    """Measured AND+AND+POPC lane-op rate of the current GPU (roofline denominator)."""
+    v = C.c_double()
+    n = C.c_int()
+    st = _load().kclique_int_peak(C.byref(v), C.byref(n), _stream(stream))
+    if st != KC_OK:
+        raise KCliqueError(st, "kclique_int_peak")
+    return {"lane_ops_per_s": float(v.value), "sms": int(n.value)}
