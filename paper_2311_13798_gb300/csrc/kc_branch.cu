@@ -63,7 +63,7 @@ struct Args {
     u32 warp_bytes;
     u32 t_max;
     u32 flags;
-    u32 pad;
+    u32 prof;           // 1: accumulate per-section cycles (KC_PROFILE)
     unsigned long long *ticket_ctr;
     u32 *d_out;
     u64 cap;
@@ -163,13 +163,13 @@ template <int W>
 __host__ __device__ constexpr u32 align16(u32 x) { return (x + 15u) & ~15u; }
 
 template <int W>
-__host__ __device__ u32 lay_bytes(u32 D) {
+__host__ __device__ u32 lay_bytes(u32 D, bool sum) {
     const u32 S = 32u * W;
     u32 b = 0;
     b += align16<W>(4u * S * W);       // A
     b += align16<W>(4u * W);           // C0
     b += align16<W>(4u * S);           // vid
-    b += align16<W>(8u * S);           // z
+    b += sum ? align16<W>(8u * S) : 0u;  // z (checksum / listing only)
     b += align16<W>(2u * S);           // col
     b += align16<W>(2u * S);           // aux
     b += align16<W>(2u * S);           // aux2
@@ -187,14 +187,14 @@ __host__ __device__ u32 lay_bytes(u32 D) {
 }
 
 template <int W>
-__device__ Lay make_lay(unsigned char *p, u32 D) {
+__device__ Lay make_lay(unsigned char *p, u32 D, bool sum) {
     const u32 S = 32u * W;
     Lay L;
     u32 o = 0;
     L.A = (u32 *)(p + o); o += align16<W>(4u * S * W);
     L.C0 = (u32 *)(p + o); o += align16<W>(4u * W);
     L.vid = (u32 *)(p + o); o += align16<W>(4u * S);
-    L.z = (u64 *)(p + o); o += align16<W>(8u * S);
+    L.z = (u64 *)(p + o); o += sum ? align16<W>(8u * S) : 0u;
     L.col = (uint16_t *)(p + o); o += align16<W>(2u * S);
     L.aux = (uint16_t *)(p + o); o += align16<W>(2u * S);
     L.aux2 = (uint16_t *)(p + o); o += align16<W>(2u * S);
@@ -229,6 +229,19 @@ __device__ __forceinline__ int warp_first_from(const u32 *X, int from, int lane)
     int fl = __ffs(bal) - 1;
     u32 wv = __shfl_sync(0xffffffffu, x, fl);
     return fl * 32 + __ffs(wv) - 1;
+}
+
+// position of the i-th set bit (i from 0) of a W-word set held in registers
+template <int W>
+__device__ __forceinline__ int select_bit(const u32 (&cw)[W], int i) {
+    int before = 0, pos = -1;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        const int p = __popc(cw[w]);
+        if (pos < 0 && i < before + p) pos = w * 32 + (int)__fns(cw[w], 0u, i - before + 1);
+        before += p;
+    }
+    return pos;
 }
 
 // permute positions: new position r holds old position ord[r] (ord in L.aux2), rows and columns,
@@ -284,30 +297,19 @@ __device__ bool permute(const Lay &L, int s, int lane, uint16_t *extra16) {
             j = sp;
         }
     }
-    // per-position arrays
-    u32 vv[W];
-    u64 zz[W];
-    uint16_t ee[W];
-#pragma unroll
-    for (int w = 0; w < W; w++) {
-        int r = 32 * w + lane;
-        if (r < s) {
-            vv[w] = L.vid[ord[r]];
-            zz[w] = L.z[ord[r]];
-            ee[w] = extra16 ? extra16[ord[r]] : 0;
-        }
-    }
+    // per-position arrays, gathered through shared scratch (the child-frame buffers,
+    // unused while a sub-branch is being renumbered); keys are recomputed from ids
+    u32 *tmp = L.childC;
+    for (int r = lane; r < s; r += 32) tmp[r] = L.vid[ord[r]];
     __syncwarp();
-#pragma unroll
-    for (int w = 0; w < W; w++) {
-        int r = 32 * w + lane;
-        if (r < s) {
-            L.vid[r] = vv[w];
-            L.z[r] = zz[w];
-            if (extra16) extra16[r] = ee[w];
-        }
-    }
+    for (int r = lane; r < s; r += 32) L.vid[r] = tmp[r];
     __syncwarp();
+    if (extra16) {
+        for (int r = lane; r < s; r += 32) tmp[r] = extra16[ord[r]];
+        __syncwarp();
+        for (int r = lane; r < s; r += 32) extra16[r] = (uint16_t)tmp[r];
+        __syncwarp();
+    }
     return true;
 }
 
@@ -320,6 +322,7 @@ struct Acc {
     u64 nodes, et;  // per lane (lane 0 counts)
     u64 ops;        // per lane: algorithmic word-ops (3 per word of an intersection, 2 per degree word)
     u64 pairs;      // per lane: adjacency tests during extraction
+    u64 sec[6];     // lane 0, profiling: extract, colour, ET (l >= 4), l=3 frames, generate, evaluate
     u32 status;
 };
 
@@ -492,37 +495,27 @@ __device__ void write_clique(u32 *out, u64 slot, u32 k, const u32 *ids, int nids
 template <int W, int MODE>
 __device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l, u64 P, int lane, Acc &acc,
                                 bool et_allowed, int ws) {
-    const int cnt = warp_popc<W>(C, lane);
+    u32 cw[W];
+    int cnt = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        cw[w] = C[w];
+        cnt += __popc(cw[w]);
+    }
     if (cnt < l) return true;
     if (!et_allowed) return false;
     const int tmax = (int)a.t_max;
-    // positions of C -> aux2
-    {
-        u32 x = lane < W ? C[lane] : 0u;
-        int c = __popc(x);
-        int off = c;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, off, o);
-            if (lane >= o) off += y;
-        }
-        off -= c;
-        while (x) {
-            int b = __ffs(x) - 1;
-            x &= x - 1;
-            L.aux2[off++] = (uint16_t)(lane * 32 + b);
-        }
-    }
-    __syncwarp();
-    // minimum degree inside C (early exit as soon as some vertex is too sparse)
+    // degrees inside C, lane per vertex (early exit as soon as some vertex is too sparse)
     int mind = cnt;
     for (int base = 0; base < cnt; base += 32) {
         int i = base + lane;
         int d = cnt;
         if (i < cnt) {
-            int x = L.aux2[i];
+            int x = select_bit<W>(cw, i);
             d = 0;
 #pragma unroll
-            for (int w = 0; w < W; w++) d += __popc(L.A[x * W + w] & C[w]);
+            for (int w = 0; w < W; w++) d += __popc(L.A[x * W + w] & cw[w]);
+            L.aux2[i] = (uint16_t)x;
             L.aux[i] = (uint16_t)d;
             acc.ops += 2u * (u32)ws;
         }
@@ -582,14 +575,116 @@ __device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l
     return true;
 }
 
+// ---------------------------------------------------------------- l = 3 frames (count only)
+// The 3-cliques of g[C]: a lane per vertex x of C computes deg(x) in C; then, whichever
+// side is sparser, either the triangles directly,
+//     sum_x sum_{y in N(x) & C, y > x} |N(x) & N(y) & C & {> y}|,
+// or by inclusion-exclusion over the missing pairs M of C (an exact identity),
+//     C(c,3) - |M| (c-2) + sum_x C(dbar(x), 2) - T(complement),
+// with dbar the missing degree and T(complement) the triples with no edge.  A
+// clique or 2-plex (Sec. 5 test, t <= t_max) is closed by the Alg. 6 count instead.
+template <int W>
+__device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, int tmax, bool use_et, int ws) {
+    u32 cw[W];
+    int cnt = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        cw[w] = C[w];
+        cnt += __popc(cw[w]);
+    }
+    if (cnt < 3) return;
+    u64 sumdeg = 0, sc2 = 0;
+    int mind = cnt, nuni = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        if (i < cnt) {
+            const int x = select_bit<W>(cw, i);
+            int d = 0;
+#pragma unroll
+            for (int w = 0; w < W; w++) d += __popc(L.A[x * W + w] & cw[w]);
+            L.aux2[i] = (uint16_t)x;
+            const int db = cnt - 1 - d;
+            sumdeg += (u64)d;
+            sc2 += (u64)db * (u64)(db - 1) / 2;
+            mind = min(mind, d);
+            nuni += (db == 0);
+            acc.ops += 2u * (u32)ws;
+        }
+    }
+    __syncwarp();
+    sumdeg = warp_sum_u64(sumdeg);
+    sc2 = warp_sum_u64(sc2);
+    mind = (int)__reduce_min_sync(0xffffffffu, (unsigned)mind);
+    nuni = (int)__reduce_add_sync(0xffffffffu, (unsigned)nuni);
+    const u64 c = (u64)cnt;
+    const u64 tri_all = c * (c - 1) * (c - 2) / 6;
+    const u64 E = sumdeg / 2, M = c * (c - 1) / 2 - E;
+    if (use_et && mind >= cnt - tmax) {
+        // clique: C(c,3); 2-plex: sum_j C(|F|, 3-j) C(p, j) 2^j (Alg. 6 count)
+        u64 add;
+        if (mind == cnt - 1) {
+            add = tri_all;
+        } else {
+            const u64 f = (u64)nuni, pp = (c - f) / 2;
+            add = f * (f - 1) * (f - 2) / 6 + (f * (f - 1) / 2) * pp * 2 + f * (pp * (pp - 1) / 2) * 4 +
+                  (pp * (pp - 1) * (pp - 2) / 6) * 8;
+        }
+        if (lane == 0) acc.leaf += add;
+        acc.et++;
+        return;
+    }
+    const bool comp = M < E;
+    u64 t = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        if (i < cnt) {
+            const int x = L.aux2[i];
+            u32 row[W];
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                const u32 ax = comp ? ~L.A[x * W + w] : L.A[x * W + w];
+                row[w] = ax & cw[w] & gt_mask(x, w);
+            }
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                u32 bits = row[w];
+                while (bits) {
+                    const int y = w * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    int tc = 0;
+#pragma unroll
+                    for (int w2 = 0; w2 < W; w2++) {
+                        const u32 ay = comp ? ~L.A[y * W + w2] : L.A[y * W + w2];
+                        tc += __popc(row[w2] & ay & gt_mask(y, w2));
+                    }
+                    t += (u64)tc;
+                    acc.ops += 3u * (u32)(ws - (y >> 5));
+                }
+            }
+        }
+    }
+    if (!comp) {
+        acc.leaf += t;
+    } else {
+        t = warp_sum_u64(t);
+        if (lane == 0) acc.leaf += tri_all - M * (c - 2) + sc2 - t;
+    }
+}
+
 // ---------------------------------------------------------------- kernel
+// resident blocks per SM targeted by the register allocator, per bitset width
+template <int W>
+struct MinBlocks {
+    static constexpr int value = W <= 4 ? 6 : (W <= 8 ? 4 : (W <= 16 ? 2 : 1));
+};
+
 template <int W, int MODE>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK_DEFAULT)
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK_DEFAULT, MinBlocks<W>::value)
 branch_kernel(Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const Lay L = make_lay<W>(smem + (size_t)wib * a.warp_bytes, a.D);
+    const Lay L = make_lay<W>(smem + (size_t)wib * a.warp_bytes, a.D, (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0);
     const bool use_rule1 = !(a.flags & KC_NO_RULE1);
     const bool use_rule2 = !(a.flags & KC_NO_RULE2);
     const bool use_et = !(a.flags & KC_NO_ET) && a.t_max >= 1;
@@ -599,6 +694,13 @@ branch_kernel(Args a) {
     Acc acc;
     acc.leaf = 0; acc.csum = 0; acc.cf = 0; acc.cf_csum = 0; acc.nodes = 0; acc.et = 0; acc.status = 0;
     acc.ops = 0; acc.pairs = 0;
+    for (int i = 0; i < 6; i++) acc.sec[i] = 0;
+    const bool prof = a.prof != 0;
+    long long tsec = 0;
+#define KC_SEC_BEGIN() \
+    if (prof) tsec = clock64()
+#define KC_SEC_END(i) \
+    if (prof && lane == 0) acc.sec[i] += (u64)(clock64() - tsec)
     u64 branches = 0;
     u128 q_total = 0;     // warp total for the current query (lane 0)
     u64 q_csum = 0;
@@ -612,6 +714,8 @@ branch_kernel(Args a) {
         if (lane == 0) {
             atomicAdd(&q.acc->word_ops, (unsigned long long)ops);
             atomicAdd(&q.acc->pair_tests, (unsigned long long)pairs);
+            if (prof)
+                for (int i = 0; i < 6; i++) atomicAdd(&q.acc->sec[i], (unsigned long long)acc.sec[i]);
             u64 lo = (u64)q_total, hi = (u64)(q_total >> 64);
             if (lo | hi) {
                 unsigned long long old = atomicAdd(&q.acc->count_lo, (unsigned long long)lo);
@@ -626,6 +730,7 @@ branch_kernel(Args a) {
         }
         q_total = 0; q_csum = 0; acc.nodes = 0; acc.et = 0; branches = 0; acc.status = 0;
         acc.ops = 0; acc.pairs = 0;
+        for (int i = 0; i < 6; i++) acc.sec[i] = 0;
     };
 
     while (true) {
@@ -680,7 +785,9 @@ branch_kernel(Args a) {
                 }
             }
         } else {
+            KC_SEC_BEGIN();
             extract<W>(L, q, s, e, q.round[e], lane, acc);
+            KC_SEC_END(0);
             if (l0 == 2) {
                 // edges of g_e
                 for (int i = lane; i < s; i += 32) {
@@ -715,9 +822,16 @@ branch_kernel(Args a) {
                     }
                 }
             } else {
-                if (colour_and_order<W>(L, s, lane) < 0) {
+                KC_SEC_BEGIN();
+                const int ncol_ok = colour_and_order<W>(L, s, lane);
+                KC_SEC_END(1);
+                if (ncol_ok < 0) {
                     acc.status |= KC_DEV_ERR_BOUNDS;
                     continue;
+                }
+                if (SUM) {
+                    for (int i = lane; i < s; i += 32) L.z[i] = zkey(L.vid[i]);
+                    __syncwarp();
                 }
                 // ---------------- A7 DFS over frames
                 if (lane < W) L.C0[lane] = lt_mask(s, lane);
@@ -733,8 +847,17 @@ branch_kernel(Args a) {
                     const u64 P = SUM ? (d == 0 ? P0 : L.childP[d * 32 + L.slot[d]]) : 0ull;
                     if (phase == 0) {
                         if (lane == 0) acc.nodes++;
+                        if (!SUM && l == 3) {
+                            KC_SEC_BEGIN();
+                            frame_l3_count<W>(L, C, lane, acc, (int)a.t_max, use_et, Ws);
+                            KC_SEC_END(3);
+                            phase = 3;
+                            continue;
+                        }
                         if (LIST) full = *(volatile unsigned long long *)&q.acc->written >= a.cap;
+                        KC_SEC_BEGIN();
                         const bool closed = early_terminate<W, MODE>(L, a, C, l, P, lane, acc, use_et && (!LIST || full), Ws);
+                        KC_SEC_END(2);
                         if (closed) { phase = 3; continue; }
                         if (lane == 0) L.cur[d] = -1;
                         if (lane < W) L.V[d * W + lane] = 0;
@@ -743,6 +866,7 @@ branch_kernel(Args a) {
                         continue;
                     }
                     if (phase == 1) {
+                        KC_SEC_BEGIN();
                         // fill a batch of up to 32 child edges (u, v)
                         const int limu = use_rule1 ? (int)L.lim[min(l, 32 * W + 1)] : s;
                         const int limv = use_rule1 ? (int)L.lim[min(l - 1, 32 * W + 1)] : s;
@@ -786,7 +910,9 @@ branch_kernel(Args a) {
                         }
                         if (lane == 0) L.cur[d] = u;
                         __syncwarp();
+                        KC_SEC_END(4);
                         if (nb == 0) { phase = 3; continue; }
+                        KC_SEC_BEGIN();
                         // evaluate the batch, lane per child
                         const int l2 = l - 2;
                         const bool has = lane < nb;
@@ -919,6 +1045,7 @@ branch_kernel(Args a) {
                             __syncwarp();
                             phase = 2;
                         }
+                        KC_SEC_END(5);
                         continue;
                     }
                     if (phase == 2) {
@@ -998,7 +1125,7 @@ kc_status launch_class(const Args &a0, const std::vector<QDesc> &qs, const kc_ru
         D = std::max(D, dq);
     }
     a.D = D;
-    a.warp_bytes = lay_bytes<W>(D);
+    a.warp_bytes = lay_bytes<W>(D, (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0);
     std::vector<u64> qstart(qs.size() + 1, 0);
     for (size_t i = 0; i < qs.size(); i++) qstart[i + 1] = qstart[i] + qs[i].nt;
     KC_CUDA(cudaMemcpyAsync(d_qs, qs.data(), sizeof(QDesc) * qs.size(), cudaMemcpyHostToDevice, s));
@@ -1087,6 +1214,7 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
     a.d_out = cfg->d_out;
     a.cap = cfg->cap;
     a.binom = g_tables[dev];
+    a.prof = getenv("KC_PROFILE") ? 1u : 0u;
     int mode = cfg->list ? MODE_LIST : ((cfg->flags & KC_CHECKSUM) ? MODE_CHECKSUM : 0);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1155,6 +1283,14 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
     cudaEventRecord(e1, s);
     if (st == KC_OK) KC_CUDA(cudaMemcpyAsync(h_acc, d_acc, sizeof(kc_dev_acc) * nq, cudaMemcpyDeviceToHost, s));
     cudaStreamSynchronize(s);
+    if (profile && st == KC_OK) {
+        const char *names[6] = {"extract", "colour", "et(l>=4)", "l3-frames", "generate", "evaluate"};
+        for (int i = 0; i < 6; i++) {
+            unsigned long long t = 0;
+            for (u32 j = 0; j < nq; j++) t += h_acc[j].sec[i];
+            fprintf(stderr, "[kclique] section %-10s %.3e warp-cycles\n", names[i], (double)t);
+        }
+    }
     cudaEventElapsedTime(ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -95,6 +95,7 @@ struct kc_dev_acc {
     unsigned long long branches;
     unsigned long long word_ops;
     unsigned long long pair_tests;
+    unsigned long long sec[6];    // profiling only: SM cycles per section (lane 0 of each warp)
     unsigned int status;
     unsigned int pad;
 };

@@ -94,6 +94,8 @@ def test_count_and_checksum(cache, name):
         got = kc().kclique_count(h, k, flags=kc().KC_CHECKSUM)
         assert got["count"] == want["count"], (name, k)
         assert got["checksum"] == want["checksum"], (name, k)
+        # count-only mode takes other kernel paths (l = 3 frames counted directly)
+        assert kc().kclique_count(h, k)["count"] == want["count"], (name, k)
         if k > tau + 2:
             assert got["count"] == 0
 
@@ -107,6 +109,7 @@ def test_ablation_flags_do_not_change_results(cache, name, flags):
         want = O.count(cg, k)
         got = K.kclique_count(h, k, flags=flags | K.KC_CHECKSUM)
         assert (got["count"], got["checksum"]) == (want["count"], want["checksum"]), (name, k, flags)
+        assert K.kclique_count(h, k, flags=flags)["count"] == want["count"], (name, k, flags)
 
 
 @pytest.mark.parametrize("t_max", [1, 2])
@@ -117,6 +120,7 @@ def test_early_termination_thresholds(cache, t_max):
             want = O.count(cg, k)
             got = kc().kclique_count(h, k, t_max=t_max, flags=kc().KC_CHECKSUM)
             assert (got["count"], got["checksum"]) == (want["count"], want["checksum"])
+            assert kc().kclique_count(h, k, t_max=t_max)["count"] == want["count"]
 
 
 def test_early_termination_fires_on_cliques_and_2plexes(cache):
@@ -170,6 +174,9 @@ def test_per_edge_counts(cache):
             ec = torch.zeros(m, dtype=torch.int64, device="cuda")
             es = torch.zeros(m, dtype=torch.int64, device="cuda")
             got = kc().kclique_count(h, k, edge_count=ec, edge_checksum=es, flags=kc().KC_CHECKSUM)
+            ec2 = torch.zeros(m, dtype=torch.int64, device="cuda")
+            kc().kclique_count(h, k, edge_count=ec2)
+            assert torch.equal(ec, ec2)
             rng = np.random.default_rng(k)
             sample = np.unique(np.concatenate([rng.choice(m, size=min(m, 150), replace=False),
                                                np.argsort(-O.vset_sizes(cg, rnd))[:20]]))
