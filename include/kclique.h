@@ -83,7 +83,12 @@ typedef struct {
     uint32_t flags;            /* KC_NO_ET | KC_NO_RULE2 | KC_CHECKSUM | KC_NO_RULE1 */
     uint64_t *d_edge_count;    /* optional device [m]: k-cliques whose first edge is e (mod 2^64) */
     uint64_t *d_edge_checksum; /* optional device [m]: their checksum */
-    uint64_t *d_edge_cycles;   /* optional device [m]: SM clock cycles the warp spent on e's sub-branch */
+    uint64_t *d_edge_cycles;   /* optional device [m]: SM clock cycles the warps spent on e's sub-branch */
+    uint32_t split_min;        /* k >= 7: sub-branches with |VSet| >= split_min are split across warps,
+                                  one work item per top-frame vertex (0 = 128; 0xFFFFFFFF = never) */
+    uint32_t pad;
+    uint64_t ticket_begin;     /* run only the top-level edges [ticket_begin, ticket_end) of the order by */
+    uint64_t ticket_end;       /* |VSet| descending (0, 0 = all): a shard for one of several GPUs */
 } kc_params;
 
 typedef struct {

@@ -88,6 +88,9 @@ kc_status run_one(const kc_graph *g, u32 k, const kc_params *p, cudaStream_t s, 
     cfg.d_edge_count = p ? p->d_edge_count : nullptr;
     cfg.d_edge_checksum = p ? p->d_edge_checksum : nullptr;
     cfg.d_edge_cycles = p ? p->d_edge_cycles : nullptr;
+    cfg.split_min = p ? p->split_min : 0u;
+    cfg.ticket_begin = p ? p->ticket_begin : 0ull;
+    cfg.ticket_end = p ? p->ticket_end : 0ull;
     kc_dev_acc acc;
     memset(&acc, 0, sizeof(acc));
     float ms = 0.f, msb = 0.f;
@@ -215,6 +218,7 @@ kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32_t *ks,
     cfg.flags = p ? p->flags : 0u;
     cfg.warps_per_block = p ? p->warps_per_block : 0u;
     cfg.blocks = p ? p->blocks : 0u;
+    cfg.split_min = p ? p->split_min : 0u;
     std::vector<kc_dev_acc> acc(qv.size());
     float ms = 0.f, msb = 0.f;
     kc_status st = kc_run_queries(qv.data(), (u32)qv.size(), &cfg, s, acc.data(), &ms, &msb);

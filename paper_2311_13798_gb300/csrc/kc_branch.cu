@@ -49,6 +49,7 @@ struct QDesc {
     u32 pad;
     u64 t0;           // first ticket (index into tickets) of this launch's range
     u64 nt;           // tickets in range
+    u64 nheavy;       // the first nheavy tickets of the range are split (k >= 7)
     kc_dev_acc *acc;
     u64 *edge_count;
     u64 *edge_checksum;
@@ -65,6 +66,14 @@ struct Args {
     u32 flags;
     u32 prof;           // 1: accumulate per-section cycles (KC_PROFILE)
     unsigned long long *ticket_ctr;
+    // splitting of heavy sub-branches (A12)
+    unsigned char *slots;           // [slot_cap] published sub-branches (nullptr: no splitting)
+    unsigned long long *slot_ctr;
+    u64 slot_cap;
+    u64 *items;                     // [item_cap] (slot << 32) | u
+    unsigned long long *item_ctr;   // items written
+    unsigned long long *item_next;  // items taken
+    u64 item_cap;
     u32 *d_out;
     u64 cap;
     const u128 *binom;
@@ -671,88 +680,388 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
     }
 }
 
-// ---------------------------------------------------------------- kernel
+// ---------------------------------------------------------------- kernels
 // resident blocks per SM targeted by the register allocator, per bitset width
 template <int W>
 struct MinBlocks {
     static constexpr int value = W <= 4 ? 6 : (W <= 8 ? 4 : (W <= 16 ? 2 : 1));
 };
 
-template <int W, int MODE>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK_DEFAULT, MinBlocks<W>::value)
-branch_kernel(Args a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const Lay L = make_lay<W>(smem + (size_t)wib * a.warp_bytes, a.D, (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0);
-    const bool use_rule1 = !(a.flags & KC_NO_RULE1);
-    const bool use_rule2 = !(a.flags & KC_NO_RULE2);
-    const bool use_et = !(a.flags & KC_NO_ET) && a.t_max >= 1;
-    constexpr bool SUM = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
-    constexpr bool LIST = (MODE & MODE_LIST) != 0;
+// A heavy sub-branch published for splitting (A12): the coloured, renumbered
+// adjacency of g_e plus what a helper warp needs to rebuild its frames.
+struct SlotHdr {
+    u32 e, s, qi, pad;
+    u64 P0, pad2;
+};
 
-    Acc acc;
-    acc.leaf = 0; acc.csum = 0; acc.cf = 0; acc.cf_csum = 0; acc.nodes = 0; acc.et = 0; acc.status = 0;
-    acc.ops = 0; acc.pairs = 0;
+template <int W>
+__host__ __device__ constexpr u32 slot_bytes() {
+    return 32u + 4u * (32u * W) * W + 4u * (32u * W) + 2u * (32u * W) + ((2u * (32u * W + 2) + 15u) & ~15u) +
+           8u * W;
+}
+
+struct WarpTotals {
+    u128 q_total;   // warp-uniform: count of the current query
+    u64 q_csum;     // warp-uniform: checksum of the current query
+    u64 branches;
+    int cur_q;
+};
+
+template <int MODE>
+__device__ void flush_query(const Args &a, Acc &acc, WarpTotals &wt, int lane, bool prof) {
+    constexpr bool SUM = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
+    if (wt.cur_q < 0) return;
+    const QDesc &q = a.qs[wt.cur_q];
+    const u64 ops = warp_sum_u64(acc.ops), pairs = warp_sum_u64(acc.pairs);
+    if (lane == 0) {
+        atomicAdd(&q.acc->word_ops, (unsigned long long)ops);
+        atomicAdd(&q.acc->pair_tests, (unsigned long long)pairs);
+        if (prof)
+            for (int i = 0; i < 6; i++) atomicAdd(&q.acc->sec[i], (unsigned long long)acc.sec[i]);
+        u64 lo = (u64)wt.q_total, hi = (u64)(wt.q_total >> 64);
+        if (lo | hi) {
+            unsigned long long old = atomicAdd(&q.acc->count_lo, (unsigned long long)lo);
+            unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+            if (hi + carry) atomicAdd(&q.acc->count_hi, (unsigned long long)(hi + carry));
+        }
+        if (SUM) atomicAdd(&q.acc->checksum, (unsigned long long)wt.q_csum);
+        atomicAdd(&q.acc->nodes, (unsigned long long)acc.nodes);
+        atomicAdd(&q.acc->et_hits, (unsigned long long)acc.et);
+        atomicAdd(&q.acc->branches, (unsigned long long)wt.branches);
+        if (acc.status) atomicOr(&q.acc->status, acc.status);
+    }
+    wt.q_total = 0; wt.q_csum = 0; wt.branches = 0;
+    acc.nodes = 0; acc.et = 0; acc.status = 0; acc.ops = 0; acc.pairs = 0;
     for (int i = 0; i < 6; i++) acc.sec[i] = 0;
-    const bool prof = a.prof != 0;
-    long long tsec = 0;
+}
+
+__device__ __forceinline__ void reset_unit(Acc &acc) {
+    acc.leaf = 0; acc.csum = 0; acc.cf = 0; acc.cf_csum = 0;
+}
+
+// end of a unit of work (a whole sub-branch, or one split item) of edge e: fold the
+// unit's count into the warp totals and add it to the optional per-edge outputs
+template <int MODE>
+__device__ void finish_unit(const QDesc &q, u32 e, Acc &acc, WarpTotals &wt, int lane, long long t_start) {
+    constexpr bool SUM = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
+    u128 leaf = warp_sum_u128(acc.leaf);
+    u64 cs = SUM ? warp_sum_u64(acc.csum) + acc.cf_csum : 0ull;
+    u128 tot = leaf + acc.cf;
+    if (tot < leaf || acc.cf == SAT128) acc.status |= KC_DEV_ERR_OVERFLOW;
+    u128 nt = wt.q_total + tot;
+    if (nt < wt.q_total) acc.status |= KC_DEV_ERR_OVERFLOW;
+    wt.q_total = nt;
+    wt.q_csum += cs;
+    if (lane == 0) {
+        if (q.edge_count && tot) atomicAdd((unsigned long long *)&q.edge_count[e], (unsigned long long)(u64)tot);
+        if (q.edge_checksum && cs) atomicAdd((unsigned long long *)&q.edge_checksum[e], (unsigned long long)cs);
+        if (q.edge_cycles) atomicAdd((unsigned long long *)&q.edge_cycles[e], (unsigned long long)(clock64() - t_start));
+    }
+}
+
 #define KC_SEC_BEGIN() \
     if (prof) tsec = clock64()
 #define KC_SEC_END(i) \
     if (prof && lane == 0) acc.sec[i] += (u64)(clock64() - tsec)
-    u64 branches = 0;
-    u128 q_total = 0;     // warp total for the current query (lane 0)
-    u64 q_csum = 0;
-    int cur_q = -1;
 
-    auto flush_query = [&](int qi) {
-        // q_total / q_csum are lane-uniform here
-        if (qi < 0) return;
-        const QDesc &q = a.qs[qi];
-        const u64 ops = warp_sum_u64(acc.ops), pairs = warp_sum_u64(acc.pairs);
-        if (lane == 0) {
-            atomicAdd(&q.acc->word_ops, (unsigned long long)ops);
-            atomicAdd(&q.acc->pair_tests, (unsigned long long)pairs);
-            if (prof)
-                for (int i = 0; i < 6; i++) atomicAdd(&q.acc->sec[i], (unsigned long long)acc.sec[i]);
-            u64 lo = (u64)q_total, hi = (u64)(q_total >> 64);
-            if (lo | hi) {
-                unsigned long long old = atomicAdd(&q.acc->count_lo, (unsigned long long)lo);
-                unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-                if (hi + carry) atomicAdd(&q.acc->count_hi, (unsigned long long)(hi + carry));
+// A7-A9: depth-first search over the frames of one sub-branch whose coloured,
+// renumbered adjacency is in L.  The top frame is C0 = {0..s-1} with l = l0; its
+// child edges (u, v) are restricted to u in [u_lo, u_hi).  top_et: run the early
+// termination test on the top frame (false when a split item resumes it).
+template <int W, int MODE>
+__device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int l0, u64 P0, int lane, Acc &acc,
+                        int Ws, int u_lo, int u_hi, bool top_et, bool prof) {
+    constexpr bool SUM = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
+    constexpr bool LIST = (MODE & MODE_LIST) != 0;
+    const bool use_rule1 = !(a.flags & KC_NO_RULE1);
+    const bool use_rule2 = !(a.flags & KC_NO_RULE2);
+    const bool use_et = !(a.flags & KC_NO_ET) && a.t_max >= 1;
+    const u32 k = q.k;
+    long long tsec = 0;
+    if (lane < W) L.C0[lane] = lt_mask(s, lane);
+    if (lane == 0) { L.cur[0] = u_lo - 1; L.slot[0] = 0; }
+    if (lane < W) L.V[lane] = 0;
+    __syncwarp();
+    int d = 0;
+    int phase = top_et ? 0 : 1;  // 0 start frame, 1 generate, 2 descend into children, 3 frame done
+    bool full = LIST && (*(volatile unsigned long long *)&q.acc->written >= a.cap);
+    while (true) {
+        const int l = l0 - 2 * d;
+        const u32 *C = d == 0 ? L.C0 : L.childC + ((size_t)(d * 32 + L.slot[d])) * W;
+        const u64 P = SUM ? (d == 0 ? P0 : L.childP[d * 32 + L.slot[d]]) : 0ull;
+        if (phase == 0) {
+            if (lane == 0) acc.nodes++;
+            if (!SUM && l == 3) {
+                KC_SEC_BEGIN();
+                frame_l3_count<W>(L, C, lane, acc, (int)a.t_max, use_et, Ws);
+                KC_SEC_END(3);
+                phase = 3;
+                continue;
             }
-            if (SUM) atomicAdd(&q.acc->checksum, (unsigned long long)q_csum);
-            atomicAdd(&q.acc->nodes, (unsigned long long)acc.nodes);
-            atomicAdd(&q.acc->et_hits, (unsigned long long)acc.et);
-            atomicAdd(&q.acc->branches, (unsigned long long)branches);
-            if (acc.status) atomicOr(&q.acc->status, acc.status);
+            if (LIST) full = *(volatile unsigned long long *)&q.acc->written >= a.cap;
+            KC_SEC_BEGIN();
+            const bool closed = early_terminate<W, MODE>(L, a, C, l, P, lane, acc, use_et && (!LIST || full), Ws);
+            KC_SEC_END(2);
+            if (closed) { phase = 3; continue; }
+            if (lane == 0) L.cur[d] = d == 0 ? u_lo - 1 : -1;
+            if (lane < W) L.V[d * W + lane] = 0;
+            __syncwarp();
+            phase = 1;
+            continue;
         }
-        q_total = 0; q_csum = 0; acc.nodes = 0; acc.et = 0; branches = 0; acc.status = 0;
-        acc.ops = 0; acc.pairs = 0;
-        for (int i = 0; i < 6; i++) acc.sec[i] = 0;
-    };
+        if (phase == 1) {
+            KC_SEC_BEGIN();
+            // fill a batch of up to 32 child edges (u, v); Rule (1) as colour prefixes
+            int limu = use_rule1 ? (int)L.lim[min(l, 32 * W + 1)] : s;
+            if (d == 0) limu = min(limu, u_hi);
+            const int limv = use_rule1 ? (int)L.lim[min(l - 1, 32 * W + 1)] : s;
+            int nb = 0;
+            u32 *V = L.V + d * W;
+            int u = L.cur[d];
+            while (nb < 32) {
+                u32 vw = lane < W ? V[lane] : 0u;
+                int c = __popc(vw);
+                int tot = __reduce_add_sync(0xffffffffu, (unsigned)c);
+                if (tot == 0) {
+                    if (u == -2) break;  // generator exhausted
+                    int nu = warp_first_from<W>(C, u + 1, lane);
+                    if (nu < 0 || nu >= limu) { u = -2; break; }
+                    u = nu;
+                    u32 nv = 0;
+                    if (lane < W) nv = L.A[u * W + lane] & C[lane] & gt_mask(u, lane) & lt_mask(limv, lane);
+                    if (lane < W) V[lane] = nv;
+                    __syncwarp();
+                    continue;
+                }
+                int off = c;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(0xffffffffu, off, o);
+                    if (lane >= o) off += y;
+                }
+                off -= c;
+                int room = 32 - nb;
+                int take = max(0, min(c, room - off));
+                for (int i = 0; i < take; i++) {
+                    int b = __ffs(vw) - 1;
+                    vw &= vw - 1;
+                    L.bu[nb + off + i] = (uint16_t)u;
+                    L.bv[nb + off + i] = (uint16_t)(lane * 32 + b);
+                }
+                if (lane < W) V[lane] = vw;
+                nb += min(tot, room);
+                __syncwarp();
+            }
+            if (lane == 0) L.cur[d] = u;
+            __syncwarp();
+            KC_SEC_END(4);
+            if (nb == 0) { phase = 3; continue; }
+            KC_SEC_BEGIN();
+            // evaluate the batch, lane per child
+            const int l2 = l - 2;
+            const bool has = lane < nb;
+            const int cu = has ? L.bu[lane] : 0;
+            const int cv = has ? L.bv[lane] : 0;
+            u32 cw[W];
+            int cc = 0;
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                u32 x = has ? (C[w] & L.A[cu * W + w] & L.A[cv * W + w] & gt_mask(cv, w)) : 0u;
+                cw[w] = x;
+                cc += __popc(x);
+            }
+            const u64 Pc = SUM ? P * L.z[cu] * L.z[cv] : 0ull;
+            if (has) acc.ops += 3u * (u32)(Ws - (cv >> 5));
+            bool push = false;
+            if (l2 == 1) {
+                acc.leaf += (u64)cc;
+                if (SUM && cc) {
+                    u64 zs = 0;
+#pragma unroll
+                    for (int w = 0; w < W; w++) {
+                        u32 x = cw[w];
+                        while (x) { int b = __ffs(x) - 1; x &= x - 1; zs += L.z[w * 32 + b]; }
+                    }
+                    acc.csum += Pc * zs;
+                }
+                if (LIST && !full) {
+                    unsigned long long base = 0;
+                    int off2 = cc;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        int y = __shfl_up_sync(0xffffffffu, off2, o);
+                        if (lane >= o) off2 += y;
+                    }
+                    int tot2 = __shfl_sync(0xffffffffu, off2, 31);
+                    off2 -= cc;
+                    if (lane == 0 && tot2) base = atomicAdd(&q.acc->written, (unsigned long long)tot2);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    u32 ids[KC_MAX_K];
+                    int np = 2 * (d + 1);
+                    for (int i = 0; i < np; i++) ids[i] = L.path[i];
+                    ids[np] = L.vid[cu];
+                    ids[np + 1] = L.vid[cv];
+                    int idx = 0;
+#pragma unroll
+                    for (int w = 0; w < W; w++) {
+                        u32 x = cw[w];
+                        while (x) {
+                            int b = __ffs(x) - 1;
+                            x &= x - 1;
+                            if (base + off2 + idx < a.cap) {
+                                ids[np + 2] = L.vid[w * 32 + b];
+                                write_clique(a.d_out, base + off2 + idx, k, ids, np + 3);
+                            }
+                            idx++;
+                        }
+                    }
+                }
+            } else if (l2 == 2) {
+                if (cc >= 2) {
+                    u64 ec = 0, zs = 0;
+#pragma unroll
+                    for (int w = 0; w < W; w++) {
+                        u32 x = cw[w];
+                        while (x) {
+                            int b = __ffs(x) - 1;
+                            x &= x - 1;
+                            const int xp = w * 32 + b;
+                            acc.ops += 3u * (u32)(Ws - (xp >> 5));
+                            u64 zin = 0;
+#pragma unroll
+                            for (int w2 = 0; w2 < W; w2++) {
+                                u32 y = L.A[xp * W + w2] & cw[w2] & gt_mask(xp, w2);
+                                ec += __popc(y);
+                                if (SUM) {
+                                    while (y) { int b2 = __ffs(y) - 1; y &= y - 1; zin += L.z[w2 * 32 + b2]; }
+                                }
+                            }
+                            if (SUM) zs += L.z[xp] * zin;
+                        }
+                    }
+                    acc.leaf += ec;
+                    if (SUM) acc.csum += Pc * zs;
+                    if (LIST && !full && ec) {
+                        unsigned long long base = atomicAdd(&q.acc->written, (unsigned long long)ec);
+                        u32 ids[KC_MAX_K];
+                        int np = 2 * (d + 1);
+                        for (int i = 0; i < np; i++) ids[i] = L.path[i];
+                        ids[np] = L.vid[cu];
+                        ids[np + 1] = L.vid[cv];
+                        u64 idx = 0;
+                        for (int w = 0; w < W; w++) {
+                            u32 x = cw[w];
+                            while (x) {
+                                int b = __ffs(x) - 1;
+                                x &= x - 1;
+                                const int xp = w * 32 + b;
+                                for (int w2 = 0; w2 < W; w2++) {
+                                    u32 y = L.A[xp * W + w2] & cw[w2] & gt_mask(xp, w2);
+                                    while (y) {
+                                        int b2 = __ffs(y) - 1;
+                                        y &= y - 1;
+                                        if (base + idx < a.cap) {
+                                            ids[np + 2] = L.vid[xp];
+                                            ids[np + 3] = L.vid[w2 * 32 + b2];
+                                            write_clique(a.d_out, base + idx, k, ids, np + 4);
+                                        }
+                                        idx++;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+            } else {
+                push = has && cc >= l2 && (!use_rule2 || distinct_colours<W>(cw, L.J, L.E) >= l2);
+            }
+            const unsigned pb = __ballot_sync(0xffffffffu, push);
+            if (pb) {
+                const int slotc = __popc(pb & ((1u << lane) - 1));
+                const int dn = d + 1;
+                if (push) {
+                    u32 *dst = L.childC + ((size_t)(dn * 32 + slotc)) * W;
+#pragma unroll
+                    for (int w = 0; w < W; w++) dst[w] = cw[w];
+                    if (SUM) L.childP[dn * 32 + slotc] = Pc;
+                    L.childUV[dn * 32 + slotc] = (u32)cu | ((u32)cv << 16);
+                }
+                if (lane == 0) { L.nchild[dn] = __popc(pb); L.nextc[dn] = 0; }
+                __syncwarp();
+                phase = 2;
+            }
+            KC_SEC_END(5);
+            continue;
+        }
+        if (phase == 2) {
+            const int dn = d + 1;
+            const int nx = L.nextc[dn];
+            if (nx < L.nchild[dn]) {
+                if (lane == 0) {
+                    L.nextc[dn] = nx + 1;
+                    L.slot[dn] = nx;
+                    if (LIST) {
+                        u32 uv = L.childUV[dn * 32 + nx];
+                        L.path[2 * dn] = L.vid[uv & 0xFFFFu];
+                        L.path[2 * dn + 1] = L.vid[uv >> 16];
+                    }
+                }
+                __syncwarp();
+                d = dn;
+                phase = 0;
+            } else {
+                phase = 1;
+            }
+            continue;
+        }
+        // phase 3: frame done
+        if (d == 0) break;
+        d--;
+        phase = 2;
+    }
+}
+
+// A5-A12, one warp per ticket.  Tickets of the split list (heavy sub-branches, k >= 7)
+// are extracted and coloured here, then published with one work item per top-frame
+// vertex u for branch_items_kernel; all other tickets run to completion here.
+template <int W, int MODE>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK_DEFAULT, MinBlocks<W>::value)
+branch_kernel(Args a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr bool SUM = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
+    constexpr bool LIST = (MODE & MODE_LIST) != 0;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const Lay L = make_lay<W>(smem + (size_t)wib * a.warp_bytes, a.D, SUM);
+    const bool use_et = !(a.flags & KC_NO_ET) && a.t_max >= 1;
+    const bool use_rule1 = !(a.flags & KC_NO_RULE1);
+    const bool prof = a.prof != 0;
+    long long tsec = 0;
+    Acc acc;
+    reset_unit(acc);
+    acc.nodes = 0; acc.et = 0; acc.status = 0; acc.ops = 0; acc.pairs = 0;
+    for (int i = 0; i < 6; i++) acc.sec[i] = 0;
+    WarpTotals wt;
+    wt.q_total = 0; wt.q_csum = 0; wt.branches = 0; wt.cur_q = -1;
 
     while (true) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(a.ticket_ctr, 1ull);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= a.qstart[a.nq]) break;
-        // find the query of ticket t
         int lo = 0, hi = (int)a.nq - 1;
         while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (a.qstart[mid] <= t) lo = mid; else hi = mid - 1; }
         const int qi = lo;
-        if (qi != cur_q) { flush_query(cur_q); cur_q = qi; }
+        if (qi != wt.cur_q) { flush_query<MODE>(a, acc, wt, lane, prof); wt.cur_q = qi; }
         const QDesc &q = a.qs[qi];
         const u32 k = q.k;
         const int l0 = (int)k - 2;
-        const u32 e = q.tickets[q.t0 + (t - a.qstart[qi])];
+        const u64 tq = t - a.qstart[qi];
+        const u32 e = q.tickets[q.t0 + tq];
         const long long t_start = clock64();
         const u64 vb = q.vset_ptr[e];
         const int s = (int)(q.vset_ptr[e + 1] - vb);
         if (s < l0) continue;
         if (s > 32 * W) { acc.status |= KC_DEV_ERR_WIDTH; continue; }
-        branches++;
+        wt.branches++;
         const int Ws = (s + 31) >> 5;  // words a sub-branch of s vertices needs
         const u32 eu = q.eu[e], ev = q.ev[e];
         const u64 P0 = SUM ? zkey(eu) * zkey(ev) : 0ull;
@@ -763,7 +1072,7 @@ branch_kernel(Args a) {
         }
         if (lane == 0) { L.path[0] = eu; L.path[1] = ev; }
         __syncwarp();
-        acc.leaf = 0; acc.csum = 0; acc.cf = 0; acc.cf_csum = 0;
+        reset_unit(acc);
         const bool full0 = LIST && (*(volatile unsigned long long *)&q.acc->written >= a.cap);
 
         if (l0 == 1) {
@@ -833,264 +1142,119 @@ branch_kernel(Args a) {
                     for (int i = lane; i < s; i += 32) L.z[i] = zkey(L.vid[i]);
                     __syncwarp();
                 }
-                // ---------------- A7 DFS over frames
-                if (lane < W) L.C0[lane] = lt_mask(s, lane);
-                if (lane == 0) { L.cur[0] = -1; L.slot[0] = 0; }
-                if (lane < W) L.V[lane] = 0;
-                __syncwarp();
-                int d = 0;
-                int phase = 0;  // 0 start frame, 1 generate, 2 descend into children, 3 frame done
-                bool full = full0;
-                while (true) {
-                    const int l = l0 - 2 * d;
-                    const u32 *C = d == 0 ? L.C0 : L.childC + ((size_t)(d * 32 + L.slot[d])) * W;
-                    const u64 P = SUM ? (d == 0 ? P0 : L.childP[d * 32 + L.slot[d]]) : 0ull;
-                    if (phase == 0) {
-                        if (lane == 0) acc.nodes++;
-                        if (!SUM && l == 3) {
-                            KC_SEC_BEGIN();
-                            frame_l3_count<W>(L, C, lane, acc, (int)a.t_max, use_et, Ws);
-                            KC_SEC_END(3);
-                            phase = 3;
-                            continue;
+                const bool heavy = !LIST && a.slots != nullptr && l0 >= 5 && tq < q.nheavy;
+                bool done = false;
+                if (heavy) {
+                    // top frame test here, once; the item kernel resumes at its child edges
+                    if (lane < W) L.C0[lane] = lt_mask(s, lane);
+                    __syncwarp();
+                    if (lane == 0) acc.nodes++;
+                    KC_SEC_BEGIN();
+                    const bool closed = early_terminate<W, MODE>(L, a, L.C0, l0, P0, lane, acc, use_et, Ws);
+                    KC_SEC_END(2);
+                    const int limu = min(s, use_rule1 ? (int)L.lim[min(l0, 32 * W + 1)] : s);
+                    if (closed || limu <= 0) {
+                        done = true;
+                    } else {
+                        unsigned long long sl = 0, ib = 0;
+                        if (lane == 0) {
+                            sl = atomicAdd(a.slot_ctr, 1ull);
+                            ib = sl < a.slot_cap ? atomicAdd(a.item_ctr, (unsigned long long)limu) : ~0ull;
                         }
-                        if (LIST) full = *(volatile unsigned long long *)&q.acc->written >= a.cap;
-                        KC_SEC_BEGIN();
-                        const bool closed = early_terminate<W, MODE>(L, a, C, l, P, lane, acc, use_et && (!LIST || full), Ws);
-                        KC_SEC_END(2);
-                        if (closed) { phase = 3; continue; }
-                        if (lane == 0) L.cur[d] = -1;
-                        if (lane < W) L.V[d * W + lane] = 0;
-                        __syncwarp();
-                        phase = 1;
-                        continue;
-                    }
-                    if (phase == 1) {
-                        KC_SEC_BEGIN();
-                        // fill a batch of up to 32 child edges (u, v)
-                        const int limu = use_rule1 ? (int)L.lim[min(l, 32 * W + 1)] : s;
-                        const int limv = use_rule1 ? (int)L.lim[min(l - 1, 32 * W + 1)] : s;
-                        int nb = 0;
-                        u32 *V = L.V + d * W;
-                        int u = L.cur[d];
-                        while (nb < 32) {
-                            u32 vw = lane < W ? V[lane] : 0u;
-                            int c = __popc(vw);
-                            int tot = __reduce_add_sync(0xffffffffu, (unsigned)c);
-                            if (tot == 0) {
-                                if (u == -2) break;  // generator exhausted
-                                // next u in C with position < limu
-                                int nu = warp_first_from<W>(C, u + 1, lane);
-                                if (nu < 0 || nu >= limu) { u = -2; break; }
-                                u = nu;
-                                u32 nv = 0;
-                                if (lane < W)
-                                    nv = L.A[u * W + lane] & C[lane] & gt_mask(u, lane) & lt_mask(limv, lane);
-                                if (lane < W) V[lane] = nv;
-                                __syncwarp();
-                                continue;
-                            }
-                            int off = c;
-                            for (int o = 1; o < 32; o <<= 1) {
-                                int y = __shfl_up_sync(0xffffffffu, off, o);
-                                if (lane >= o) off += y;
-                            }
-                            off -= c;
-                            int room = 32 - nb;
-                            int take = max(0, min(c, room - off));
-                            for (int i = 0; i < take; i++) {
-                                int b = __ffs(vw) - 1;
-                                vw &= vw - 1;
-                                L.bu[nb + off + i] = (uint16_t)u;
-                                L.bv[nb + off + i] = (uint16_t)(lane * 32 + b);
-                            }
-                            if (lane < W) V[lane] = vw;
-                            nb += min(tot, room);
-                            __syncwarp();
-                        }
-                        if (lane == 0) L.cur[d] = u;
-                        __syncwarp();
-                        KC_SEC_END(4);
-                        if (nb == 0) { phase = 3; continue; }
-                        KC_SEC_BEGIN();
-                        // evaluate the batch, lane per child
-                        const int l2 = l - 2;
-                        const bool has = lane < nb;
-                        const int cu = has ? L.bu[lane] : 0;
-                        const int cv = has ? L.bv[lane] : 0;
-                        u32 cw[W];
-                        int cc = 0;
-#pragma unroll
-                        for (int w = 0; w < W; w++) {
-                            u32 x = has ? (C[w] & L.A[cu * W + w] & L.A[cv * W + w] & gt_mask(cv, w)) : 0u;
-                            cw[w] = x;
-                            cc += __popc(x);
-                        }
-                        const u64 Pc = SUM ? P * L.z[cu] * L.z[cv] : 0ull;
-                        if (has) acc.ops += 3u * (u32)(Ws - (cv >> 5));
-                        bool push = false;
-                        if (l2 == 1) {
-                            acc.leaf += (u64)cc;
-                            if (SUM && cc) {
-                                u64 zs = 0;
-#pragma unroll
-                                for (int w = 0; w < W; w++) {
-                                    u32 x = cw[w];
-                                    while (x) { int b = __ffs(x) - 1; x &= x - 1; zs += L.z[w * 32 + b]; }
-                                }
-                                acc.csum += Pc * zs;
-                            }
-                            if (LIST && !full) {
-                                unsigned long long base = 0;
-                                int off2 = cc;
-                                for (int o = 1; o < 32; o <<= 1) {
-                                    int y = __shfl_up_sync(0xffffffffu, off2, o);
-                                    if (lane >= o) off2 += y;
-                                }
-                                int tot2 = __shfl_sync(0xffffffffu, off2, 31);
-                                off2 -= cc;
-                                if (lane == 0 && tot2) base = atomicAdd(&q.acc->written, (unsigned long long)tot2);
-                                base = __shfl_sync(0xffffffffu, base, 0);
-                                u32 ids[KC_MAX_K];
-                                int np = 2 * (d + 1);
-                                for (int i = 0; i < np; i++) ids[i] = L.path[i];
-                                ids[np] = L.vid[cu];
-                                ids[np + 1] = L.vid[cv];
-                                int idx = 0;
-#pragma unroll
-                                for (int w = 0; w < W; w++) {
-                                    u32 x = cw[w];
-                                    while (x) {
-                                        int b = __ffs(x) - 1;
-                                        x &= x - 1;
-                                        if (base + off2 + idx < a.cap) {
-                                            ids[np + 2] = L.vid[w * 32 + b];
-                                            write_clique(a.d_out, base + off2 + idx, k, ids, np + 3);
-                                        }
-                                        idx++;
-                                    }
-                                }
-                            }
-                        } else if (l2 == 2) {
-                            if (cc >= 2) {
-                                u64 ec = 0, zs = 0;
-#pragma unroll
-                                for (int w = 0; w < W; w++) {
-                                    u32 x = cw[w];
-                                    while (x) {
-                                        int b = __ffs(x) - 1;
-                                        x &= x - 1;
-                                        const int xp = w * 32 + b;
-                                        acc.ops += 3u * (u32)(Ws - (xp >> 5));
-                                        u64 zin = 0;
-#pragma unroll
-                                        for (int w2 = 0; w2 < W; w2++) {
-                                            u32 y = L.A[xp * W + w2] & cw[w2] & gt_mask(xp, w2);
-                                            ec += __popc(y);
-                                            if (SUM) {
-                                                while (y) { int b2 = __ffs(y) - 1; y &= y - 1; zin += L.z[w2 * 32 + b2]; }
-                                            }
-                                        }
-                                        if (SUM) zs += L.z[xp] * zin;
-                                    }
-                                }
-                                acc.leaf += ec;
-                                if (SUM) acc.csum += Pc * zs;
-                                if (LIST && !full && ec) {
-                                    unsigned long long base = atomicAdd(&q.acc->written, (unsigned long long)ec);
-                                    u32 ids[KC_MAX_K];
-                                    int np = 2 * (d + 1);
-                                    for (int i = 0; i < np; i++) ids[i] = L.path[i];
-                                    ids[np] = L.vid[cu];
-                                    ids[np + 1] = L.vid[cv];
-                                    u64 idx = 0;
-                                    for (int w = 0; w < W; w++) {
-                                        u32 x = cw[w];
-                                        while (x) {
-                                            int b = __ffs(x) - 1;
-                                            x &= x - 1;
-                                            const int xp = w * 32 + b;
-                                            for (int w2 = 0; w2 < W; w2++) {
-                                                u32 y = L.A[xp * W + w2] & cw[w2] & gt_mask(xp, w2);
-                                                while (y) {
-                                                    int b2 = __ffs(y) - 1;
-                                                    y &= y - 1;
-                                                    if (base + idx < a.cap) {
-                                                        ids[np + 2] = L.vid[xp];
-                                                        ids[np + 3] = L.vid[w2 * 32 + b2];
-                                                        write_clique(a.d_out, base + idx, k, ids, np + 4);
-                                                    }
-                                                    idx++;
-                                                }
-                                            }
-                                        }
-                                    }
-                                }
-                            }
-                        } else {
-                            push = has && cc >= l2 && (!use_rule2 || distinct_colours<W>(cw, L.J, L.E) >= l2);
-                        }
-                        const unsigned pb = __ballot_sync(0xffffffffu, push);
-                        if (pb) {
-                            const int slotc = __popc(pb & ((1u << lane) - 1));
-                            const int dn = d + 1;
-                            if (push) {
-                                u32 *dst = L.childC + ((size_t)(dn * 32 + slotc)) * W;
-#pragma unroll
-                                for (int w = 0; w < W; w++) dst[w] = cw[w];
-                                if (SUM) L.childP[dn * 32 + slotc] = Pc;
-                                L.childUV[dn * 32 + slotc] = (u32)cu | ((u32)cv << 16);
-                            }
-                            if (lane == 0) { L.nchild[dn] = __popc(pb); L.nextc[dn] = 0; }
-                            __syncwarp();
-                            phase = 2;
-                        }
-                        KC_SEC_END(5);
-                        continue;
-                    }
-                    if (phase == 2) {
-                        const int dn = d + 1;
-                        const int nx = L.nextc[dn];
-                        if (nx < L.nchild[dn]) {
+                        sl = __shfl_sync(0xffffffffu, sl, 0);
+                        ib = __shfl_sync(0xffffffffu, ib, 0);
+                        if (sl < a.slot_cap && ib + (u64)limu <= a.item_cap) {
+                            unsigned char *gs = a.slots + sl * (u64)slot_bytes<W>();
                             if (lane == 0) {
-                                L.nextc[dn] = nx + 1;
-                                L.slot[dn] = nx;
-                                u32 uv = L.childUV[dn * 32 + nx];
-                                L.path[2 * dn] = L.vid[uv & 0xFFFFu];
-                                L.path[2 * dn + 1] = L.vid[uv >> 16];
+                                SlotHdr h;
+                                h.e = e; h.s = (u32)s; h.qi = (u32)qi; h.pad = 0; h.P0 = P0; h.pad2 = 0;
+                                *(SlotHdr *)gs = h;
                             }
-                            __syncwarp();
-                            d = dn;
-                            phase = 0;
-                        } else {
-                            phase = 1;
+                            u32 *gA = (u32 *)(gs + 32);
+                            u32 *gvid = gA + (32 * W) * W;
+                            uint16_t *gcol = (uint16_t *)(gvid + 32 * W);
+                            uint16_t *glim = gcol + 32 * W;
+                            u32 *gJ = (u32 *)((unsigned char *)glim + ((2u * (32u * W + 2) + 15u) & ~15u));
+                            for (int i = lane; i < s * W; i += 32) gA[i] = L.A[i];
+                            for (int i = lane; i < s; i += 32) { gvid[i] = L.vid[i]; gcol[i] = L.col[i]; }
+                            for (int i = lane; i < 32 * W + 2; i += 32) glim[i] = L.lim[i];
+                            if (lane < W) { gJ[lane] = L.J[lane]; gJ[W + lane] = L.E[lane]; }
+                            for (int u = lane; u < limu; u += 32) a.items[ib + u] = (sl << 32) | (u64)u;
+                            done = true;
                         }
-                        continue;
+                        // else: no room left, run the sub-branch here (below)
                     }
-                    // phase 3: frame done
-                    if (d == 0) break;
-                    d--;
-                    phase = 2;
                 }
+                if (!done) run_dfs<W, MODE>(L, a, q, s, l0, P0, lane, acc, Ws, 0, s, !heavy, prof);
             }
         }
-        // ---------------- end of ticket: totals
-        u128 leaf = warp_sum_u128(acc.leaf);
-        u64 cs = SUM ? warp_sum_u64(acc.csum) + acc.cf_csum : 0ull;
-        u128 tot = leaf + acc.cf;
-        if (tot < leaf || acc.cf == SAT128) acc.status |= KC_DEV_ERR_OVERFLOW;
-        u128 nt = q_total + tot;
-        if (nt < q_total) acc.status |= KC_DEV_ERR_OVERFLOW;
-        q_total = nt;
-        q_csum += cs;
-        if (lane == 0) {
-            if (q.edge_count) q.edge_count[e] = (u64)tot;
-            if (q.edge_checksum) q.edge_checksum[e] = cs;
-            if (q.edge_cycles) q.edge_cycles[e] = (u64)(clock64() - t_start);
-        }
+        finish_unit<MODE>(q, e, acc, wt, lane, t_start);
     }
-    flush_query(cur_q);
+    flush_query<MODE>(a, acc, wt, lane, prof);
 }
+
+// A12 work items of split sub-branches: (slot, u) -> the child edges (u, v) of the top
+// frame of that sub-branch and everything below them.
+template <int W, int MODE>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK_DEFAULT, MinBlocks<W>::value)
+branch_items_kernel(Args a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr bool SUM = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const Lay L = make_lay<W>(smem + (size_t)wib * a.warp_bytes, a.D, SUM);
+    const bool prof = a.prof != 0;
+    Acc acc;
+    reset_unit(acc);
+    acc.nodes = 0; acc.et = 0; acc.status = 0; acc.ops = 0; acc.pairs = 0;
+    for (int i = 0; i < 6; i++) acc.sec[i] = 0;
+    WarpTotals wt;
+    wt.q_total = 0; wt.q_csum = 0; wt.branches = 0; wt.cur_q = -1;
+    const u64 n_items = *(volatile unsigned long long *)a.item_ctr;
+    long long cached = -1;
+    while (true) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(a.item_next, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items || it >= a.item_cap) break;
+        const u64 item = a.items[it];
+        const u64 sl = item >> 32;
+        const int u = (int)(item & 0xFFFFFFFFull);
+        const unsigned char *gs = a.slots + sl * (u64)slot_bytes<W>();
+        const SlotHdr h = *(const SlotHdr *)gs;
+        const int qi = (int)h.qi;
+        if (qi != wt.cur_q) { flush_query<MODE>(a, acc, wt, lane, prof); wt.cur_q = qi; }
+        const QDesc &q = a.qs[qi];
+        const int s = (int)h.s;
+        const int l0 = (int)q.k - 2;
+        const int Ws = (s + 31) >> 5;
+        const long long t_start = clock64();
+        if ((long long)sl != cached) {
+            const u32 *gA = (const u32 *)(gs + 32);
+            const u32 *gvid = gA + (32 * W) * W;
+            const uint16_t *gcol = (const uint16_t *)(gvid + 32 * W);
+            const uint16_t *glim = gcol + 32 * W;
+            const u32 *gJ = (const u32 *)((const unsigned char *)glim + ((2u * (32u * W + 2) + 15u) & ~15u));
+            for (int i = lane; i < s * W; i += 32) L.A[i] = gA[i];
+            for (int i = lane; i < s; i += 32) {
+                L.vid[i] = gvid[i];
+                L.col[i] = gcol[i];
+                if (SUM) L.z[i] = zkey(gvid[i]);
+            }
+            for (int i = lane; i < 32 * W + 2; i += 32) L.lim[i] = glim[i];
+            if (lane < W) { L.J[lane] = gJ[lane]; L.E[lane] = gJ[W + lane]; }
+            if (lane == 0) { L.path[0] = q.eu[h.e]; L.path[1] = q.ev[h.e]; }
+            __syncwarp();
+            cached = (long long)sl;
+        }
+        reset_unit(acc);
+        run_dfs<W, MODE>(L, a, q, s, l0, h.P0, lane, acc, Ws, u, u + 1, false, prof);
+        finish_unit<MODE>(q, h.e, acc, wt, lane, t_start);
+    }
+    flush_query<MODE>(a, acc, wt, lane, prof);
+}
+#undef KC_SEC_BEGIN
+#undef KC_SEC_END
 
 // ---------------------------------------------------------------- binomials
 __global__ void binom_kernel(u128 *T) {
@@ -1114,15 +1278,51 @@ __global__ void binom_kernel(u128 *T) {
 
 std::vector<u128 *> g_tables;  // per device
 
+// launch geometry for a persistent kernel: (blocks, warps per block, shared bytes)
+template <typename K>
+kc_status geometry(K kern, u32 warp_bytes, u64 work, const kc_run_cfg *cfg, u64 *blocks, int *wpb_out, size_t *smem_out) {
+    int wpb = WARPS_PER_BLOCK_DEFAULT;
+    size_t smem = (size_t)warp_bytes * wpb;
+    int dev = 0, max_optin = 0, nsm = 0;
+    KC_CUDA(cudaGetDevice(&dev));
+    KC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    KC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    while (smem > (size_t)max_optin && wpb > 1) { wpb--; smem = (size_t)warp_bytes * wpb; }
+    if (smem > (size_t)max_optin) return KC_ERR_UNSUPPORTED;
+    KC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, smem));
+    if (per_sm < 1) per_sm = 1;
+    u64 bl = (u64)nsm * per_sm;
+    if (cfg->blocks) bl = cfg->blocks;
+    u64 need = kc_div_up(work, (u64)wpb);
+    if (bl > need) bl = need;
+    if (bl < 1) bl = 1;
+    *blocks = bl;
+    *wpb_out = wpb;
+    *smem_out = smem;
+    return KC_OK;
+}
+
+// device buffers of the split path, grown on demand and reused across classes
+struct SplitBufs {
+    unsigned char *slots = nullptr;
+    u64 slot_bytes_cap = 0;
+    u64 *items = nullptr;
+    u64 item_cap = 0;
+};
+
 template <int W, int MODE>
 kc_status launch_class(const Args &a0, const std::vector<QDesc> &qs, const kc_run_cfg *cfg, cudaStream_t s,
-                       QDesc *d_qs, u64 *d_qstart, unsigned long long *d_ctr) {
+                       QDesc *d_qs, u64 *d_qstart, unsigned long long *d_ctr, SplitBufs *sb) {
     Args a = a0;
     u32 D = 1;
+    u64 nheavy = 0;
     for (const QDesc &q : qs) {
         int l0 = (int)q.k - 2;
         u32 dq = l0 >= 3 ? (u32)((l0 - 3) / 2 + 1) + 1 : 1;
         D = std::max(D, dq);
+        nheavy += q.nheavy;
     }
     a.D = D;
     a.warp_bytes = lay_bytes<W>(D, (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0);
@@ -1130,45 +1330,62 @@ kc_status launch_class(const Args &a0, const std::vector<QDesc> &qs, const kc_ru
     for (size_t i = 0; i < qs.size(); i++) qstart[i + 1] = qstart[i] + qs[i].nt;
     KC_CUDA(cudaMemcpyAsync(d_qs, qs.data(), sizeof(QDesc) * qs.size(), cudaMemcpyHostToDevice, s));
     KC_CUDA(cudaMemcpyAsync(d_qstart, qstart.data(), sizeof(u64) * qstart.size(), cudaMemcpyHostToDevice, s));
-    KC_CUDA(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), s));
+    KC_CUDA(cudaMemsetAsync(d_ctr, 0, 4 * sizeof(unsigned long long), s));
     a.qs = d_qs;
     a.qstart = d_qstart;
     a.nq = (u32)qs.size();
     a.ticket_ctr = d_ctr;
-    int wpb = WARPS_PER_BLOCK_DEFAULT;
-    size_t smem = (size_t)a.warp_bytes * wpb;
-    int dev = 0;
-    KC_CUDA(cudaGetDevice(&dev));
-    int max_optin = 0, nsm = 0;
-    KC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    KC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    while (smem > (size_t)max_optin && wpb > 1) { wpb--; smem = (size_t)a.warp_bytes * wpb; }
-    if (smem > (size_t)max_optin) return KC_ERR_UNSUPPORTED;
-    KC_CUDA(cudaFuncSetAttribute(branch_kernel<W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, branch_kernel<W, MODE>, 32 * wpb, smem));
-    if (per_sm < 1) per_sm = 1;
-    u64 total = qstart.back();
-    u64 blocks = (u64)nsm * per_sm;
-    if (cfg->blocks) blocks = cfg->blocks;
-    u64 need = kc_div_up(total, (u64)wpb);
-    if (blocks > need) blocks = need;
-    if (blocks < 1) blocks = 1;
+    a.slots = nullptr;
+    if (nheavy && !(MODE & MODE_LIST)) {
+        const u64 need_slots = nheavy * (u64)slot_bytes<W>();
+        const u64 need_items = nheavy * 32ull * W;
+        if (sb->slot_bytes_cap < need_slots) {
+            if (sb->slots) KC_CUDA(cudaFreeAsync(sb->slots, s));
+            sb->slots = nullptr;
+            KC_CUDA(cudaMallocAsync(&sb->slots, need_slots, s));
+            sb->slot_bytes_cap = need_slots;
+        }
+        if (sb->item_cap < need_items) {
+            if (sb->items) KC_CUDA(cudaFreeAsync(sb->items, s));
+            sb->items = nullptr;
+            KC_CUDA(cudaMallocAsync(&sb->items, need_items * sizeof(u64), s));
+            sb->item_cap = need_items;
+        }
+        a.slots = sb->slots;
+        a.slot_cap = nheavy;
+        a.items = sb->items;
+        a.item_cap = need_items;
+        a.slot_ctr = d_ctr + 1;
+        a.item_ctr = d_ctr + 2;
+        a.item_next = d_ctr + 3;
+    }
+    u64 blocks = 1;
+    int wpb = 1;
+    size_t smem = 0;
+    kc_status st = geometry(branch_kernel<W, MODE>, a.warp_bytes, qstart.back(), cfg, &blocks, &wpb, &smem);
+    if (st != KC_OK) return st;
     branch_kernel<W, MODE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
     KC_CUDA(cudaGetLastError());
+    if (a.slots) {
+        // the item count is only known on the device: size the grid for a full machine
+        st = geometry(branch_items_kernel<W, MODE>, a.warp_bytes, ~0ull >> 8, cfg, &blocks, &wpb, &smem);
+        if (st != KC_OK) return st;
+        branch_items_kernel<W, MODE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
+        KC_CUDA(cudaGetLastError());
+    }
     return KC_OK;
 }
 
 template <int MODE>
 kc_status launch_mode(int W, const Args &a, const std::vector<QDesc> &qs, const kc_run_cfg *cfg, cudaStream_t s,
-                      QDesc *d_qs, u64 *d_qstart, unsigned long long *d_ctr) {
+                      QDesc *d_qs, u64 *d_qstart, unsigned long long *d_ctr, SplitBufs *sb) {
     switch (W) {
-        case 1: return launch_class<1, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr);
-        case 2: return launch_class<2, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr);
-        case 4: return launch_class<4, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr);
-        case 8: return launch_class<8, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr);
-        case 16: return launch_class<16, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr);
-        case 32: return launch_class<32, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr);
+        case 1: return launch_class<1, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr, sb);
+        case 2: return launch_class<2, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr, sb);
+        case 4: return launch_class<4, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr, sb);
+        case 8: return launch_class<8, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr, sb);
+        case 16: return launch_class<16, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr, sb);
+        case 32: return launch_class<32, MODE>(a, qs, cfg, s, d_qs, d_qstart, d_ctr, sb);
     }
     return KC_ERR_UNSUPPORTED;
 }
@@ -1180,6 +1397,12 @@ kc_status kc_ensure_tables(cudaStream_t s) {
     KC_CUDA(cudaGetDevice(&dev));
     if ((int)g_tables.size() <= dev) g_tables.resize(dev + 1, nullptr);
     if (!g_tables[dev]) {
+        // keep stream-ordered scratch (split buffers, prepare temporaries) cached in the pool
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
         u128 *T = nullptr;
         KC_CUDA(cudaMalloc(&T, sizeof(u128) * BINOM_N * BINOM_R));
         binom_kernel<<<1, 64, 0, s>>>(T);
@@ -1206,7 +1429,8 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
     KC_CUDA(cudaMemsetAsync(d_acc, 0, sizeof(kc_dev_acc) * (nq ? nq : 1), s));
     KC_CUDA(cudaMallocAsync(&d_qs, sizeof(QDesc) * (nq ? nq : 1), s));
     KC_CUDA(cudaMallocAsync(&d_qstart, sizeof(u64) * (nq + 1), s));
-    KC_CUDA(cudaMallocAsync(&d_ctr, sizeof(unsigned long long), s));
+    KC_CUDA(cudaMallocAsync(&d_ctr, 4 * sizeof(unsigned long long), s));
+    SplitBufs sb;
     Args a;
     memset(&a, 0, sizeof(a));
     a.t_max = cfg->t_max;
@@ -1242,6 +1466,10 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
             if (s_lo < k - 2) s_lo = k - 2;
             if (s_lo > s_hi) continue;
             u64 b = suffix(s_hi + 1), en = suffix(s_lo);
+            if (cfg->ticket_end > cfg->ticket_begin) {  // shard
+                b = std::max<u64>(b, cfg->ticket_begin);
+                en = std::min<u64>(en, cfg->ticket_end);
+            }
             if (en <= b) continue;
             QDesc d;
             memset(&d, 0, sizeof(d));
@@ -1251,6 +1479,12 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
             d.k = k;
             d.t0 = b;
             d.nt = en - b;
+            // split the heavy tickets (|VSet| >= split_min) of k >= 7 queries (A12)
+            const u64 smin = cfg->split_min ? cfg->split_min : 128ull;
+            if (k >= 7 && cfg->split_min != ~0u) {
+                const u64 hb = suffix(std::max<u64>(smin, s_lo));
+                d.nheavy = hb > b ? std::min<u64>(hb - b, d.nt) : 0ull;
+            }
             d.acc = d_acc + i;
             d.edge_count = cfg->d_edge_count;
             d.edge_checksum = cfg->d_edge_checksum;
@@ -1262,9 +1496,9 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
         cudaEventCreate(&b0);
         cudaEventCreate(&b1);
         cudaEventRecord(b0, s);
-        if (mode == 0) st = launch_mode<0>(W, a, qs, cfg, s, d_qs, d_qstart, d_ctr);
-        else if (mode == MODE_CHECKSUM) st = launch_mode<MODE_CHECKSUM>(W, a, qs, cfg, s, d_qs, d_qstart, d_ctr);
-        else st = launch_mode<MODE_LIST | MODE_CHECKSUM>(W, a, qs, cfg, s, d_qs, d_qstart, d_ctr);
+        if (mode == 0) st = launch_mode<0>(W, a, qs, cfg, s, d_qs, d_qstart, d_ctr, &sb);
+        else if (mode == MODE_CHECKSUM) st = launch_mode<MODE_CHECKSUM>(W, a, qs, cfg, s, d_qs, d_qstart, d_ctr, &sb);
+        else st = launch_mode<MODE_LIST | MODE_CHECKSUM>(W, a, qs, cfg, s, d_qs, d_qstart, d_ctr, &sb);
         cudaEventRecord(b1, s);
         // the query table is reused by the next class: wait for this launch to read it
         if (st == KC_OK) KC_CUDA(cudaStreamSynchronize(s));
@@ -1298,6 +1532,8 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
     cudaFreeAsync(d_qs, s);
     cudaFreeAsync(d_qstart, s);
     cudaFreeAsync(d_ctr, s);
+    if (sb.slots) cudaFreeAsync(sb.slots, s);
+    if (sb.items) cudaFreeAsync(sb.items, s);
     cudaStreamSynchronize(s);
     if (st == KC_OK) {
         cudaError_t ce = cudaGetLastError();

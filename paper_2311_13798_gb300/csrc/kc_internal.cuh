@@ -83,6 +83,8 @@ struct kc_run_cfg {
     u64 *d_edge_count;
     u64 *d_edge_checksum;
     u64 *d_edge_cycles;
+    u32 split_min;      // 0: default; ~0u: never split
+    u64 ticket_begin, ticket_end;  // shard of the ticket order (0, 0 = all)
 };
 
 // Accumulators in device memory (one per query).

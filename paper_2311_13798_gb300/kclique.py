@@ -37,7 +37,8 @@ KC_NO_RULE1 = 0x8
 class KcParams(C.Structure):
     _fields_ = [("t_max", C.c_uint32), ("warps_per_block", C.c_uint32), ("blocks", C.c_uint32),
                 ("flags", C.c_uint32), ("d_edge_count", C.c_void_p), ("d_edge_checksum", C.c_void_p),
-                ("d_edge_cycles", C.c_void_p)]
+                ("d_edge_cycles", C.c_void_p), ("split_min", C.c_uint32), ("pad", C.c_uint32),
+                ("ticket_begin", C.c_uint64), ("ticket_end", C.c_uint64)]
 
 
 class KcResult(C.Structure):
@@ -175,8 +176,10 @@ def kclique_prepare(row_ptr, col, n: int | None = None, stream=None) -> Graph:
 
 
 def _params(t_max=0, flags=0, blocks=0, warps_per_block=0, edge_count=None, edge_checksum=None,
-            edge_cycles=None):
+            edge_cycles=None, split_min=0, ticket_begin=0, ticket_end=0):
     p = KcParams()
+    p.split_min = split_min
+    p.ticket_begin, p.ticket_end = ticket_begin, ticket_end
     p.t_max, p.flags, p.blocks, p.warps_per_block = t_max, flags, blocks, warps_per_block
     p.d_edge_count = edge_count.data_ptr() if edge_count is not None else None
     p.d_edge_checksum = edge_checksum.data_ptr() if edge_checksum is not None else None

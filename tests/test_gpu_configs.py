@@ -1,0 +1,113 @@
+"""GPU parity on the benchmark workloads (full size where the oracle's stored values
+exist, scaled otherwise), through the C ABI, exact integer equality.
+
+* G(2000, 0.01): counts and listing against the oracle at run time.
+* Chung-Lu power law, n = 1e6 (the bench workload, launched as bench.py launches
+  it): graph fingerprint, tau, peel rounds, triangles, and the k = 5 and 7 counts and
+  checksums against tests/golden/configs.json (written by oracle/make_golden.py).
+* SBM with exact 2-plex blocks (dense-core stress), scaled to 80-vertex blocks so the
+  oracle finishes: whole-graph counts; every 2-plex block against its closed form.
+* A batch of uneven small graphs with their own k: kclique_count_batch against the
+  oracle per graph and against one kclique_count per graph.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import graphs as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "configs.json")))
+
+
+def K():
+    from paper_2311_13798_gb300 import kclique
+    return kclique
+
+
+def prep(g):
+    rp = torch.from_numpy(g.row_ptr.astype(np.int32)).cuda()
+    col = torch.from_numpy(g.col.astype(np.int32)).cuda()
+    return K().kclique_prepare(rp, col, g.n)
+
+
+def test_config1_gnp_2000():
+    g = G.config1()
+    assert g.fingerprint() == GOLD["c1/graph"]["fingerprint"]
+    h = prep(g)
+    for k in (3, 4):
+        got = K().kclique_count(h, k, flags=K().KC_CHECKSUM)
+        assert str(got["count"]) == GOLD[f"c1/k{k}"]["count"]
+        assert str(got["checksum"]) == GOLD[f"c1/k{k}"]["checksum"]
+    want = O.list_cliques(g, 3).astype(np.int64)
+    out = torch.full((len(want) + 5, 3), -1, dtype=torch.int32, device="cuda")
+    r = K().kclique_list(h, 3, out)
+    rows = out[: r["written"]].cpu().numpy().astype(np.int64)
+    assert sorted(map(tuple, rows.tolist())) == sorted(map(tuple, want.tolist()))
+
+
+@pytest.fixture(scope="module")
+def power_law():
+    g = G.chung_lu()
+    return g, prep(g)
+
+
+def test_config2_power_law_prepare(power_law):
+    g, h = power_law
+    ref = GOLD["c2/graph"]
+    assert g.fingerprint() == ref["fingerprint"], "generator mismatch, not a parity failure"
+    info = K().kclique_info(h)
+    assert info["m"] == ref["m"] and info["tau"] == ref["tau"] and info["rounds"] == ref["rounds"]
+    assert info["triangles"] == int(ref["triangles"])
+
+
+@pytest.mark.parametrize("k", [5, 7])
+def test_config2_power_law_counts(power_law, k):
+    g, h = power_law
+    key = f"c2/k{k}"
+    if key not in GOLD:
+        pytest.skip(f"{key} not computed by oracle/make_golden.py")
+    got = K().kclique_count(h, k, flags=K().KC_CHECKSUM)
+    assert str(got["count"]) == GOLD[key]["count"]
+    assert str(got["checksum"]) == GOLD[key]["checksum"]
+    assert str(K().kclique_count(h, k)["count"]) == GOLD[key]["count"]
+
+
+def test_config3_sbm_2plex_scaled():
+    g, info = G.sbm_2plex(blocks=24, block_size=80, p_in=0.9, p_out=2e-3, two_plex_blocks=6, seed=0)
+    h = prep(g)
+    for k in (5, 6, 7):
+        want = O.count(g, k)
+        got = K().kclique_count(h, k, flags=K().KC_CHECKSUM)
+        assert (got["count"], got["checksum"]) == (want["count"], want["checksum"])
+        assert K().kclique_count(h, k)["count"] == want["count"]
+    # each 2-plex block alone: the closed form of Alg. 6 (f universal, p missing pairs)
+    blk = info["block_of"]
+    u, v = g.edges()
+    for b in info["two_plex_blocks"][:3]:
+        keep = (blk[u] == b) & (blk[v] == b)
+        sub = G.from_edges(g.n, u[keep], v[keep])
+        p = info["matching"][b]
+        f = 80 - 2 * p
+        hb = prep(sub)
+        for k in (6, 9, 12):
+            want = sum(math.comb(f, k - j) * math.comb(p, j) * 2**j for j in range(0, k + 1))
+            assert K().kclique_count(hb, k)["count"] == want
+
+
+def test_config4_batch_of_uneven_graphs():
+    specs = G.batch_specs(count=48, seed=3, n_hi=600)
+    graphs = [G.batch_graph(s) for s in specs]
+    hs = [prep(g) for g in graphs]
+    ks = [s["k"] for s in specs]
+    res = K().kclique_count_batch(hs, ks, flags=K().KC_CHECKSUM)
+    for g, h, k, r in zip(graphs, hs, ks, res):
+        want = O.count(g, k)
+        assert (r["count"], r["checksum"]) == (want["count"], want["checksum"])
+        single = K().kclique_count(h, k, flags=K().KC_CHECKSUM)
+        assert (single["count"], single["checksum"]) == (r["count"], r["checksum"])

@@ -270,3 +270,38 @@ def test_large_counts_exceed_64_bits():
     got = K.kclique_count(h, 20, flags=K.KC_CHECKSUM)
     assert got["count"] == math.comb(200, 20)
     assert got["checksum"] == O.count(G.complete(200), 20)["checksum"]
+
+
+@pytest.mark.parametrize("name", ["gnp120_dense", "k70", "two_plex", "t3plex", "chung_lu", "sbm", "turan"])
+def test_split_sub_branches_match(cache, name):
+    """Heavy sub-branches split into per-vertex work items (forced with a tiny
+    split_min) give the same counts, checksums and per-edge counts as unsplit runs."""
+    g, cg, h = get(cache, name)
+    K = kc()
+    _, rnd, _ = O.truss_peel(cg)
+    for k in (7, 8, 9):
+        want = O.count(cg, k)
+        for split_min in (3, 16, 0xFFFFFFFF):
+            got = K.kclique_count(h, k, split_min=split_min, flags=K.KC_CHECKSUM)
+            assert (got["count"], got["checksum"]) == (want["count"], want["checksum"]), (name, k, split_min)
+            assert K.kclique_count(h, k, split_min=split_min)["count"] == want["count"]
+        ec = torch.zeros(g.m, dtype=torch.int64, device="cuda")
+        K.kclique_count(h, k, split_min=3, edge_count=ec)
+        sample = np.argsort(-O.vset_sizes(cg, rnd))[:25]
+        cnt, _ = O.edge_counts(cg, k, rnd, sample)
+        assert [int(x) for x in ec.cpu().numpy().view(np.uint64)[sample]] == cnt
+
+
+def test_ticket_shards_add_up(cache):
+    """Disjoint shards of the ticket order (one per GPU of a multi-GPU run) sum to the whole."""
+    K = kc()
+    for name in ("chung_lu", "sbm", "gnp120_dense"):
+        g, cg, h = get(cache, name)
+        m = g.m
+        for k in (4, 5, 7):
+            whole = K.kclique_count(h, k, flags=K.KC_CHECKSUM)
+            cuts = [0, 3, 40, m // 3, m]
+            parts = [K.kclique_count(h, k, ticket_begin=a, ticket_end=b, flags=K.KC_CHECKSUM)
+                     for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+            assert sum(p["count"] for p in parts) == whole["count"]
+            assert sum(p["checksum"] for p in parts) % (1 << 64) == whole["checksum"]
