@@ -31,7 +31,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-KS = (5, 7, 9)
+# k = 9 on this graph holds ~1e16-1e17 cliques; the paper's ET (t <= 2) leaves billions of
+# small frames and one pass takes tens of minutes, so the default step runs k = 5 and 7
+# (see the design doc for the k = 9 shard measurements); --ks 5,7,9 runs all three.
+KS = (5, 7)
 LIST_K = 5
 LIST_CAP = 1 << 24
 METRIC = "k-cliques/s (exact)"
@@ -219,6 +222,7 @@ def main(argv=None):
     for _ in range(args.warmup):
         res, lst = step()
     torch.cuda.synchronize()
+    K.kclique_launch_count(reset=True)
     if world > 1:
         dist.barrier()
     sampler = ClockSampler(local)
@@ -227,6 +231,7 @@ def main(argv=None):
     times, cliques = [], 0
     phase = {"prepare": 0.0, "count": 0.0}
     branch_ms = {k: 0.0 for k in ks}
+    word_ops = {k: 0 for k in ks}
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -239,11 +244,13 @@ def main(argv=None):
         cliques += sum(r["count"] for r in res.values())
         phase["prepare"] += lst["ms_prepare"]
         for k, r in res.items():
-            branch_ms[k] += r["ms_count"]
+            branch_ms[k] += r["ms_branch"]
+            word_ops[k] += r["word_ops"]
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
+    launches = K.kclique_launch_count()
     my_ms = sum(times)
     if world > 1:
         t = torch.tensor([my_ms], dtype=torch.float64, device="cuda")
@@ -259,18 +266,45 @@ def main(argv=None):
     if not args.no_e2e:
         rp_h = torch.from_numpy(g.row_ptr.astype(np.int32)).pin_memory()
         col_h = torch.from_numpy(g.col.astype(np.int32)).pin_memory()
-        step(True, rp_h.numpy(), col_h.numpy())
+        step(True, rp_h, col_h)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         n_e2e, c_e2e = max(1, min(args.steps, 2)), 0
         for _ in range(n_e2e):
-            res, lst = step(True, rp_h.numpy(), col_h.numpy())
+            res, lst = step(True, rp_h, col_h)
             c_e2e += sum(r["count"] for r in res.values())
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         e2e = {"value": c_e2e / el, "unit": "k-cliques/s",
                "h2d_bytes_per_step": int(4 * (g.n + 1) + 4 * g.col.size),
                "d2h_bytes_per_step": int(72 * (len(ks) + 1))}
+
+    # roofline of the dominant kernel (the branch kernels of kclique_count): algorithmic
+    # bitset lane-ops (3 per word of every candidate-set intersection, 2 per word of every
+    # degree test, counted in-kernel) over their CUDA-event time, against the measured
+    # AND+AND+POPC peak of this GPU
+    peak = K.kclique_int_peak()["lane_ops_per_s"]
+    ops_all, ms_all = sum(word_ops.values()), sum(branch_ms.values())
+    achieved = ops_all / (ms_all / 1e3) if ms_all else 0.0
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        tj = json.load(open(tpath))
+        if tj.get("kernel_rev") == K.kclique_kernel_rev():
+            traffic = tj.get("bytes_per_launch")
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "G lane-ops/s",
+            "frac": achieved / peak if peak else None, "traffic": traffic,
+            "kernel": "branch_kernel + branch_items_kernel (all width classes), measured live with CUDA events",
+            "peak_kind": "measured AND+AND+POPC microbenchmark (kclique_int_peak) on this GPU"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        tot_c, tot_s, tops, thr = 0, 0.0, 0, 1
+        for k in ks:
+            r = cpu_oracle_rate(g, k, args.cpu_seconds / len(ks), seed=k)
+            tot_c += r["cliques"]; tot_s += r["seconds"]; tops += r["tops"]; thr = r["threads"]
+        cpu = {"value": tot_c / tot_s if tot_s else 0.0, "unit": "k-cliques/s", "cores": thr, "kind": "oracle",
+               "sample": f"{tops} random top vertices of the oracle's degeneracy-ordered vertex branching "
+                         f"on the same graph, k in {ks}, {tot_s:.1f} s of CPU time"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "k-cliques/s", "n_gpus": world, "steps": args.steps,
@@ -282,7 +316,8 @@ def main(argv=None):
                            "ms_prepare": phase["prepare"] / args.steps,
                            "ms_count": {k: v / args.steps for k, v in branch_ms.items()},
                            "counts": {k: str(r["count"]) for k, r in res.items()}},
-                "clocks": clocks, "e2e": e2e}
+                "clocks": clocks, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+                "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -185,6 +185,14 @@ KC_API kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32
  */
 KC_API kc_status kclique_int_peak(double *lane_ops_per_s, int *sms, kc_stream s);
 
+/* kclique_launch_count -- measurement utility: GPU kernels this library has launched in
+ * this process (reset != 0: return the count and restart it at zero). */
+KC_API unsigned long long kclique_launch_count(int reset);
+
+/* kclique_kernel_rev -- measurement utility: a hash of the kernel sources this library
+ * was built from, to tell whether stored profiler counters still describe it. */
+KC_API const char *kclique_kernel_rev(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,8 +37,18 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def kernel_rev() -> str:
+    """Short hash of the CUDA sources (identifies the kernels behind stored ncu counters)."""
+    import hashlib
+    h = hashlib.sha256()
+    for src in SOURCES + ["kc_internal.cuh"]:
+        h.update(open(os.path.join(CSRC, src), "rb").read())
+    return h.hexdigest()[:12]
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(OUT, exist_ok=True)
+    extra = list(extra or []) + [f'-DKC_KERNEL_REV="{kernel_rev()}"']
     headers = [os.path.join(CSRC, "kc_internal.cuh"), os.path.join(HERE, "..", "include", "kclique.h")]
     objs = []
     jobs = []

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "kc_internal.cuh"
@@ -15,6 +16,19 @@ void kc_set_last_cuda_error(cudaError_t e, const char *what, const char *file, i
 }
 
 extern "C" const char *kclique_last_error(void) { return g_last_error; }
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void kc_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" unsigned long long kclique_launch_count(int reset) {
+    return reset ? g_launches.exchange(0) : g_launches.load();
+}
+
+#ifndef KC_KERNEL_REV
+#define KC_KERNEL_REV "unknown"
+#endif
+extern "C" const char *kclique_kernel_rev(void) { return KC_KERNEL_REV; }
 
 namespace {
 

@@ -580,7 +580,7 @@ __device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l
     if (add == SAT128) acc.status |= KC_DEV_ERR_OVERFLOW;
     acc.cf = add_sat(acc.cf, add);
     acc.cf_csum += csum;
-    acc.et++;
+    if (lane == 0) acc.et++;
     return true;
 }
 
@@ -638,8 +638,7 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
             add = f * (f - 1) * (f - 2) / 6 + (f * (f - 1) / 2) * pp * 2 + f * (pp * (pp - 1) / 2) * 4 +
                   (pp * (pp - 1) * (pp - 2) / 6) * 8;
         }
-        if (lane == 0) acc.leaf += add;
-        acc.et++;
+        if (lane == 0) { acc.leaf += add; acc.et++; }
         return;
     }
     const bool comp = M < E;
@@ -713,6 +712,7 @@ __device__ void flush_query(const Args &a, Acc &acc, WarpTotals &wt, int lane, b
     if (wt.cur_q < 0) return;
     const QDesc &q = a.qs[wt.cur_q];
     const u64 ops = warp_sum_u64(acc.ops), pairs = warp_sum_u64(acc.pairs);
+    const u64 nodes = warp_sum_u64(acc.nodes), ets = warp_sum_u64(acc.et);
     if (lane == 0) {
         atomicAdd(&q.acc->word_ops, (unsigned long long)ops);
         atomicAdd(&q.acc->pair_tests, (unsigned long long)pairs);
@@ -725,8 +725,8 @@ __device__ void flush_query(const Args &a, Acc &acc, WarpTotals &wt, int lane, b
             if (hi + carry) atomicAdd(&q.acc->count_hi, (unsigned long long)(hi + carry));
         }
         if (SUM) atomicAdd(&q.acc->checksum, (unsigned long long)wt.q_csum);
-        atomicAdd(&q.acc->nodes, (unsigned long long)acc.nodes);
-        atomicAdd(&q.acc->et_hits, (unsigned long long)acc.et);
+        atomicAdd(&q.acc->nodes, (unsigned long long)nodes);
+        atomicAdd(&q.acc->et_hits, (unsigned long long)ets);
         atomicAdd(&q.acc->branches, (unsigned long long)wt.branches);
         if (acc.status) atomicOr(&q.acc->status, acc.status);
     }
@@ -865,7 +865,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
             int cc = 0;
 #pragma unroll
             for (int w = 0; w < W; w++) {
-                u32 x = has ? (C[w] & L.A[cu * W + w] & L.A[cv * W + w] & gt_mask(cv, w)) : 0u;
+                u32 x = (has && w >= (cv >> 5)) ? (C[w] & L.A[cu * W + w] & L.A[cv * W + w] & gt_mask(cv, w)) : 0u;
                 cw[w] = x;
                 cc += __popc(x);
             }
@@ -971,7 +971,38 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                     }
                 }
             } else {
-                push = has && cc >= l2 && (!use_rule2 || distinct_colours<W>(cw, L.J, L.E) >= l2);
+                bool closed = false;
+                if (!SUM && l2 == 3 && has && cc >= 3 && use_et && cc <= 64) {
+                    // small l = 3 child: the t-plex test and the Alg. 6 count in this lane
+                    const int tmax = (int)a.t_max;
+                    const int w0 = cv >> 5;  // the child's set has no bits below v's word
+                    int nuni = 0;
+                    bool plex = true;
+#pragma unroll
+                    for (int w = 0; w < W; w++) {
+                        u32 bits = plex ? cw[w] : 0u;
+                        while (bits) {
+                            const int x = w * 32 + __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            int dg = 0;
+#pragma unroll
+                            for (int w2 = 0; w2 < W; w2++)
+                                if (w2 >= w0) dg += __popc(L.A[x * W + w2] & cw[w2]);
+                            if (dg < cc - tmax) { plex = false; bits = 0; }
+                            nuni += (dg == cc - 1);
+                        }
+                    }
+                    acc.ops += 2u * (u32)(Ws - w0) * (u32)cc;
+                    if (plex) {
+                        const u64 c = (u64)cc, f = (u64)nuni, pp = (c - f) / 2;
+                        acc.leaf += f * (f - 1) * (f - 2) / 6 + (f * (f - 1) / 2) * pp * 2 + f * (pp * (pp - 1) / 2) * 4 +
+                                    (pp * (pp - 1) * (pp - 2) / 6) * 8;
+                        acc.et++;
+                        acc.nodes++;
+                        closed = true;
+                    }
+                }
+                push = has && !closed && cc >= l2 && (!use_rule2 || distinct_colours<W>(cw, L.J, L.E) >= l2);
             }
             const unsigned pb = __ballot_sync(0xffffffffu, push);
             if (pb) {
@@ -1365,12 +1396,14 @@ kc_status launch_class(const Args &a0, const std::vector<QDesc> &qs, const kc_ru
     kc_status st = geometry(branch_kernel<W, MODE>, a.warp_bytes, qstart.back(), cfg, &blocks, &wpb, &smem);
     if (st != KC_OK) return st;
     branch_kernel<W, MODE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
+    kc_note_launch();
     KC_CUDA(cudaGetLastError());
     if (a.slots) {
         // the item count is only known on the device: size the grid for a full machine
         st = geometry(branch_items_kernel<W, MODE>, a.warp_bytes, ~0ull >> 8, cfg, &blocks, &wpb, &smem);
         if (st != KC_OK) return st;
         branch_items_kernel<W, MODE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
+        kc_note_launch();
         KC_CUDA(cudaGetLastError());
     }
     return KC_OK;
@@ -1406,6 +1439,7 @@ kc_status kc_ensure_tables(cudaStream_t s) {
         u128 *T = nullptr;
         KC_CUDA(cudaMalloc(&T, sizeof(u128) * BINOM_N * BINOM_R));
         binom_kernel<<<1, 64, 0, s>>>(T);
+        kc_note_launch();
         KC_CUDA(cudaGetLastError());
         KC_CUDA(cudaStreamSynchronize(s));
         g_tables[dev] = T;

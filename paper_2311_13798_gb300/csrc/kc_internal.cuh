@@ -21,6 +21,9 @@ typedef uint32_t u32;
 
 void kc_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 
+// host-side count of kernel launches made by the library (for the bench's launch count)
+void kc_note_launch();
+
 // device-side status word bits (set by kernels, read by the host)
 #define KC_DEV_ERR_BOUNDS 0x1u
 #define KC_DEV_ERR_OVERFLOW 0x2u

@@ -94,11 +94,14 @@ kc_status scan_excl(const TI *in, TO *out, u64 n, cudaStream_t s) {
     KC_CUDA(cudaMallocAsync(&bs, sizeof(TO) * (nb + 1), s));
     KC_CUDA(cudaMallocAsync(&bss, sizeof(TO) * (nb + 1), s));
     scan_block_kernel<TI, TO><<<(unsigned)nb, threads, 0, s>>>(in, out, bs, n);
+    kc_note_launch();
     if (nb > 1) {
         kc_status st = scan_excl<TO, TO>(bs, bss, nb, s);
         if (st != KC_OK) return st;
         scan_add_kernel<TO><<<grid_for(n), TPB, 0, s>>>(out, bss, n, per);
+        kc_note_launch();
         set_total_kernel<TO><<<1, 1, 0, s>>>(out, bss, bs, nb, n);
+        kc_note_launch();
     } else {
         KC_CUDA(cudaMemcpyAsync(out + n, bs, sizeof(TO), cudaMemcpyDeviceToDevice, s));
     }
@@ -281,15 +284,20 @@ kc_status sort_segments(const u64 *d_ptr, u32 *d_data, u64 nrows, cudaStream_t s
     KC_CUDA(cudaMallocAsync(&bin_cnt, sizeof(u32) * 4, s));
     KC_CUDA(cudaMemsetAsync(bin_cnt, 0, sizeof(u32) * 4, s));
     bin_rows_kernel<<<grid_for(nrows), TPB, 0, s>>>(d_ptr, nrows, bins, bin_cnt, lim_warp, lim_block);
+    kc_note_launch();
     u32 h_cnt[4];
     KC_CUDA(cudaMemcpyAsync(h_cnt, bin_cnt, sizeof(u32) * 4, cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaStreamSynchronize(s));
-    if (h_cnt[0]) sort_rows_warp_kernel<<<grid_for((u64)h_cnt[0] * 32), TPB, 0, s>>>(d_ptr, d_data, bins, bin_cnt);
+    if (h_cnt[0]) {
+        sort_rows_warp_kernel<<<grid_for((u64)h_cnt[0] * 32), TPB, 0, s>>>(d_ptr, d_data, bins, bin_cnt);
+        kc_note_launch();
+    }
     if (h_cnt[1]) {
         size_t sm = sizeof(u32) * lim_block;
         KC_CUDA(cudaFuncSetAttribute(sort_rows_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         unsigned nb = h_cnt[1] < 65536 ? h_cnt[1] : 65536;
         sort_rows_block_kernel<<<nb, 512, sm, s>>>(d_ptr, d_data, bins + nrows, bin_cnt + 1, lim_block);
+        kc_note_launch();
     }
     if (h_cnt[2]) {
         // longest row -> scratch size (one row at a time per block; use one block)
@@ -305,6 +313,7 @@ kc_status sort_segments(const u64 *d_ptr, u32 *d_data, u64 nrows, cudaStream_t s
         u32 *scratch = nullptr;
         KC_CUDA(cudaMallocAsync(&scratch, sizeof(u32) * P, s));
         sort_rows_global_kernel<<<1, 1024, 0, s>>>(d_ptr, d_data, bins + 2 * nrows, h_cnt[2], scratch, P);
+        kc_note_launch();
         KC_CUDA(cudaFreeAsync(scratch, s));
     }
     KC_CUDA(cudaFreeAsync(bins, s));
@@ -659,7 +668,11 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
     KC_TRY(dalloc(&d_flags, 4, s, &scr));
     KC_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(unsigned) * 4, s));
     validate_kernel<<<grid_for(std::max<u64>(n, nnz)), TPB, 0, s>>>(rp, ci, n, nnz, d_flags);
-    if (n) clean_check_kernel<<<warp_grid(n), TPB, 0, s>>>(rp, ci, n, d_flags + 1);
+    kc_note_launch();
+    if (n) {
+        clean_check_kernel<<<warp_grid(n), TPB, 0, s>>>(rp, ci, n, d_flags + 1);
+        kc_note_launch();
+    }
     unsigned h_flags[4];
     KC_CUDA(cudaMemcpyAsync(h_flags, d_flags, sizeof(h_flags), cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaStreamSynchronize(s));
@@ -684,6 +697,7 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
         KC_TRY(dalloc(&cursor, (u64)n + 1, s, &scr));
         KC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(u32) * ((u64)n + 1), s));
         sym_count_kernel<<<warp_grid(n), TPB, 0, s>>>(rp, ci, n, cnt);
+        kc_note_launch();
         KC_TRY(scan_excl<u32, u64>(cnt, tptr, n, s));
         u64 tot = 0;
         KC_CUDA(cudaMemcpyAsync(&tot, tptr + n, sizeof(u64), cudaMemcpyDeviceToHost, s));
@@ -692,8 +706,10 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
         KC_TRY(dalloc(&tcol, tot, s, &scr));
         KC_CUDA(cudaMemcpyAsync(cursor, tptr, sizeof(u64) * ((u64)n + 1), cudaMemcpyDeviceToDevice, s));
         sym_scatter_kernel<<<warp_grid(n), TPB, 0, s>>>(rp, ci, n, cursor, tcol);
+        kc_note_launch();
         KC_TRY(sort_segments(tptr, tcol, n, s));
         dedupe_count_kernel<<<warp_grid(n), TPB, 0, s>>>(tptr, tcol, n, cnt);
+        kc_note_launch();
         u64 *optr;
         KC_TRY(dalloc(&optr, (u64)n + 1, s, &scr));
         KC_TRY(scan_excl<u32, u64>(cnt, optr, n, s));
@@ -703,7 +719,9 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
         KC_TRY(dalloc(&col, nnz2, s, nullptr));
         g->col = col;
         dedupe_write_kernel<<<warp_grid(n), TPB, 0, s>>>(tptr, tcol, n, optr, col);
+        kc_note_launch();
         u64_to_u32_kernel<<<grid_for((u64)n + 1), TPB, 0, s>>>(optr, row_ptr, (u64)n + 1);
+        kc_note_launch();
     }
     g->nnz = nnz2;
     u64 m = nnz2 / 2;
@@ -727,9 +745,12 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
     KC_TRY(dalloc(&g->tickets, m, s, nullptr));
     if (n) {
         upper_count_kernel<<<grid_for(n), TPB, 0, s>>>(row_ptr, col, n, ucnt, ustart, d_maxdeg);
+        kc_note_launch();
         KC_TRY(scan_excl<u32, u64>(ucnt, eoff, n, s));
         edge_ids_upper_kernel<<<warp_grid(n), TPB, 0, s>>>(row_ptr, col, n, ustart, eoff, g->pos_eid, g->eu, g->ev);
+        kc_note_launch();
         edge_ids_lower_kernel<<<warp_grid(n), TPB, 0, s>>>(row_ptr, col, n, ustart, g->pos_eid);
+        kc_note_launch();
     }
     KC_CUDA(cudaMemcpyAsync(&g->max_degree, d_maxdeg, sizeof(u32), cudaMemcpyDeviceToHost, s));
 
@@ -744,9 +765,12 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
     KC_CUDA(cudaMemsetAsync(sup, 0, sizeof(u32) * (m ? m : 1), s));
     if (n) {
         orient_count_kernel<<<warp_grid(n), TPB, 0, s>>>(row_ptr, col, n, ocnt);
+        kc_note_launch();
         KC_TRY(scan_excl<u32, u64>(ocnt, optr2, n, s));
         orient_write_kernel<<<warp_grid(n), TPB, 0, s>>>(row_ptr, col, g->pos_eid, n, optr2, ocol, oeid);
+        kc_note_launch();
         triangles_kernel<0><<<warp_grid(n), TPB, 0, s>>>(row_ptr, col, n, optr2, ocol, oeid, sup, nullptr, nullptr);
+        kc_note_launch();
     }
     u64 *inc_ptr, *cursor2;
     KC_TRY(dalloc(&inc_ptr, m + 1, s, &scr));
@@ -758,7 +782,10 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
     u64 *inc;
     KC_TRY(dalloc(&inc, ninc, s, &scr));
     KC_CUDA(cudaMemcpyAsync(cursor2, inc_ptr, sizeof(u64) * (m + 1), cudaMemcpyDeviceToDevice, s));
-    if (n) triangles_kernel<1><<<warp_grid(n), TPB, 0, s>>>(row_ptr, col, n, optr2, ocol, oeid, nullptr, cursor2, inc);
+    if (n) {
+        triangles_kernel<1><<<warp_grid(n), TPB, 0, s>>>(row_ptr, col, n, optr2, ocol, oeid, nullptr, cursor2, inc);
+        kc_note_launch();
+    }
     g->triangles = ninc / 3;
 
     // ---- A3: level-synchronous peel
@@ -774,7 +801,10 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
     u32 *h_ctr = nullptr;
     KC_CUDA(cudaMallocHost(&h_ctr, sizeof(u32) * 4));
     struct HostFree { u32 *p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{h_ctr};
-    if (m) iota_kernel<<<grid_for(m), TPB, 0, s>>>(alive, m);
+    if (m) {
+        iota_kernel<<<grid_for(m), TPB, 0, s>>>(alive, m);
+        kc_note_launch();
+    }
     u64 nalive = m;
     u32 lvl = 0, r = 0;
     u32 nf = 0;
@@ -784,6 +814,7 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
             KC_CUDA(cudaMemsetAsync(ctr, 0, sizeof(u32) * 2, s));
             KC_CUDA(cudaMemsetAsync(ctr + 2, 0xFF, sizeof(u32), s));
             compact_alive_kernel<<<grid_for(nalive), TPB, 0, s>>>(alive, (u32)nalive, st, sup, alive2, ctr, ctr + 2);
+            kc_note_launch();
             KC_CUDA(cudaMemcpyAsync(h_ctr, ctr, sizeof(u32) * 4, cudaMemcpyDeviceToHost, s));
             KC_CUDA(cudaStreamSynchronize(s));
             nalive = h_ctr[0];
@@ -792,15 +823,19 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
             if (h_ctr[2] > lvl) lvl = h_ctr[2];
             KC_CUDA(cudaMemsetAsync(ctr + 1, 0, sizeof(u32), s));
             frontier_from_alive_kernel<<<grid_for(nalive), TPB, 0, s>>>(alive, (u32)nalive, sup, lvl, F, ctr + 1);
+            kc_note_launch();
             KC_CUDA(cudaMemcpyAsync(h_ctr + 1, ctr + 1, sizeof(u32), cudaMemcpyDeviceToHost, s));
             KC_CUDA(cudaStreamSynchronize(s));
             nf = h_ctr[1];
             if (nf == 0) return KC_ERR_CUDA;  // cannot happen: the least support is <= lvl
         }
         mark_frontier_kernel<<<grid_for(nf), TPB, 0, s>>>(F, nf, st, g->level, g->round, lvl, r);
+        kc_note_launch();
         KC_CUDA(cudaMemsetAsync(ctr + 3, 0, sizeof(u32), s));
         peel_round_kernel<<<warp_grid(nf), TPB, 0, s>>>(F, nf, inc_ptr, inc, st, sup, lvl, Fn, ctr + 3);
+        kc_note_launch();
         retire_frontier_kernel<<<grid_for(nf), TPB, 0, s>>>(F, nf, st);
+        kc_note_launch();
         KC_CUDA(cudaMemcpyAsync(h_ctr + 3, ctr + 3, sizeof(u32), cudaMemcpyDeviceToHost, s));
         KC_CUDA(cudaStreamSynchronize(s));
         nf = h_ctr[3];
@@ -812,7 +847,10 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
     // ---- A4: VSet
     u32 *vcnt;
     KC_TRY(dalloc(&vcnt, m + 1, s, &scr));
-    if (m) vset_kernel<0><<<warp_grid(m), TPB, 0, s>>>(m, inc_ptr, inc, g->round, g->eu, g->ev, vcnt, nullptr, nullptr);
+    if (m) {
+        vset_kernel<0><<<warp_grid(m), TPB, 0, s>>>(m, inc_ptr, inc, g->round, g->eu, g->ev, vcnt, nullptr, nullptr);
+        kc_note_launch();
+    }
     KC_TRY(scan_excl<u32, u64>(vcnt, g->vset_ptr, m, s));
     u64 tv = 0;
     KC_CUDA(cudaMemcpyAsync(&tv, g->vset_ptr + m, sizeof(u64), cudaMemcpyDeviceToHost, s));
@@ -821,9 +859,13 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
     KC_TRY(dalloc(&g->vset, tv, s, nullptr));
     if (m) {
         vset_kernel<1><<<warp_grid(m), TPB, 0, s>>>(m, inc_ptr, inc, g->round, g->eu, g->ev, nullptr, g->vset_ptr, g->vset);
+        kc_note_launch();
         KC_TRY(sort_segments(g->vset_ptr, g->vset, m, s));
     }
-    if (nnz2) pos_round_kernel<<<grid_for(nnz2), TPB, 0, s>>>(g->pos_eid, g->round, nnz2, g->pos_round);
+    if (nnz2) {
+        pos_round_kernel<<<grid_for(nnz2), TPB, 0, s>>>(g->pos_eid, g->round, nnz2, g->pos_round);
+        kc_note_launch();
+    }
 
     // ---- tickets by |VSet| descending
     u32 *hist, *d_maxs;
@@ -833,7 +875,10 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
     u64 hsz = (u64)g->max_degree + 2;
     KC_TRY(dalloc(&hist, hsz, s, &scr));
     KC_CUDA(cudaMemsetAsync(hist, 0, sizeof(u32) * hsz, s));
-    if (m) size_hist_kernel<<<grid_for(m), TPB, 0, s>>>(vcnt, m, hist, d_maxs);
+    if (m) {
+        size_hist_kernel<<<grid_for(m), TPB, 0, s>>>(vcnt, m, hist, d_maxs);
+        kc_note_launch();
+    }
     KC_CUDA(cudaMemcpyAsync(&g->tau, d_maxs, sizeof(u32), cudaMemcpyDeviceToHost, s));
     std::vector<u32> h_hist(hsz);
     KC_CUDA(cudaMemcpyAsync(h_hist.data(), hist, sizeof(u32) * hsz, cudaMemcpyDeviceToHost, s));
@@ -854,7 +899,10 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
     u64 *tcur;
     KC_TRY(dalloc(&tcur, hsz, s, &scr));
     KC_CUDA(cudaMemcpyAsync(tcur, h_off.data(), sizeof(u64) * hsz, cudaMemcpyHostToDevice, s));
-    if (m) ticket_scatter_kernel<<<grid_for(m), TPB, 0, s>>>(vcnt, m, tcur, g->tickets);
+    if (m) {
+        ticket_scatter_kernel<<<grid_for(m), TPB, 0, s>>>(vcnt, m, tcur, g->tickets);
+        kc_note_launch();
+    }
     KC_CUDA(cudaGetLastError());
     KC_CUDA(cudaStreamSynchronize(s));
     g->resident_bytes = sizeof(u32) * ((u64)n + 1) + sizeof(u32) * nnz2 * 3 + sizeof(u32) * m * 7 +

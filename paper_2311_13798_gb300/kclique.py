@@ -94,6 +94,10 @@ def _load():
             lib.kclique_status_string.argtypes = [C.c_int]
             lib.kclique_last_error.restype = C.c_char_p
             lib.kclique_last_error.argtypes = []
+            lib.kclique_launch_count.restype = C.c_ulonglong
+            lib.kclique_launch_count.argtypes = [C.c_int]
+            lib.kclique_kernel_rev.restype = C.c_char_p
+            lib.kclique_kernel_rev.argtypes = []
             lib.kclique_int_peak.restype = C.c_int
             lib.kclique_int_peak.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int), vp]
             lib.kclique_count_batch.restype = C.c_int
@@ -258,3 +262,12 @@ def kclique_int_peak(stream=None) -> dict:
     if st != KC_OK:
         raise KCliqueError(st, "kclique_int_peak")
     return {"lane_ops_per_s": float(v.value), "sms": int(n.value)}
+
+
+def kclique_launch_count(reset: bool = False) -> int:
+    """Kernel launches made by the library so far (optionally restarting the count)."""
+    return int(_load().kclique_launch_count(int(reset)))
+
+
+def kclique_kernel_rev() -> str:
+    return _load().kclique_kernel_rev().decode()
