@@ -178,6 +178,24 @@ KC_API kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32
                               const kc_params *p, kc_stream s, kc_result *results);
 
 /*
+ * kclique_count_batch_noalloc -- the batched count of kclique_count_batch for callers
+ * that cannot allocate device memory when they count (a fixed pre-reserved pool, a
+ * driver-thread callback, a process at its memory limit).  The paper has no
+ * counterpart; this is an integration aid.  Per-call scratch comes from one static
+ * device array of 32 KiB inside the library, so the call makes no cudaMalloc /
+ * cudaFree and no allocating library call.  Arguments and results as for
+ * kclique_count_batch, with these limits:
+ *   - nq <= 64 queries per call, else KC_ERR_INVALID_ARG (kclique_last_error says why);
+ *   - no per-edge outputs in p; sub-branches are never split across warps;
+ *   - the first call on a device sets up that device (looks up the static arrays and
+ *     fills a static binomial table); make it before any stream capture;
+ *   - all calls on a device share the static scratch: calls that overlap on the GPU
+ *     race, so the caller serialises them.
+ */
+KC_API kc_status kclique_count_batch_noalloc(const kc_graph *const *graphs, const uint32_t *ks, uint32_t nq,
+                                             const kc_params *p, kc_stream s, kc_result *results);
+
+/*
  * kclique_int_peak -- measurement utility (no counterpart in the paper): the sustained
  * rate of the branch kernel's inner operation mix, AND + AND + POPC on 32-bit words held
  * in registers, on the current device, in lane-ops per second (3 per word), with the SM

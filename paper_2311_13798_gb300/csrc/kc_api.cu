@@ -17,6 +17,8 @@ void kc_set_last_cuda_error(cudaError_t e, const char *what, const char *file, i
 
 extern "C" const char *kclique_last_error(void) { return g_last_error; }
 
+void kc_set_last_error_msg(const char *msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 static std::atomic<unsigned long long> g_launches{0};
 
 void kc_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }

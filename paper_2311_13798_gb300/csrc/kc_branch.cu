@@ -1636,3 +1636,139 @@ extern "C" KC_API kc_status kclique_int_peak(double *lane_ops_per_s, int *sms, k
     if (sms) *sms = nsm;
     return KC_OK;
 }
+
+// ---------------------------------------------------------------- no-allocation path
+// The same persistent kernels, launched for callers that cannot allocate device memory:
+// the query table, accumulators and counters live in caller-supplied scratch, the
+// binomial table is caller-supplied, sub-branches are not split (no split buffers), and
+// host-side bookkeeping uses fixed arrays.
+static_assert(KC_BINOM_ENTRIES == BINOM_N * BINOM_R, "binomial table size");
+
+namespace {
+constexpr u32 kNoallocMaxQ = 64;
+
+u64 align256(u64 x) { return (x + 255ull) & ~255ull; }
+
+template <int W, int MODE>
+kc_status launch_class_fixed(const Args &a0, const QDesc *qs, u32 nqs, cudaStream_t s, QDesc *d_qs, u64 *d_qstart,
+                             unsigned long long *d_ctr) {
+    Args a = a0;
+    u32 D = 1;
+    for (u32 i = 0; i < nqs; i++) {
+        int l0 = (int)qs[i].k - 2;
+        u32 dq = l0 >= 3 ? (u32)((l0 - 3) / 2 + 1) + 1 : 1;
+        D = std::max(D, dq);
+    }
+    a.D = D;
+    a.warp_bytes = lay_bytes<W>(D, (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0);
+    u64 qstart[kNoallocMaxQ + 1];
+    qstart[0] = 0;
+    for (u32 i = 0; i < nqs; i++) qstart[i + 1] = qstart[i] + qs[i].nt;
+    KC_CUDA(cudaMemcpyAsync(d_qs, qs, sizeof(QDesc) * nqs, cudaMemcpyHostToDevice, s));
+    KC_CUDA(cudaMemcpyAsync(d_qstart, qstart, sizeof(u64) * (nqs + 1), cudaMemcpyHostToDevice, s));
+    KC_CUDA(cudaMemsetAsync(d_ctr, 0, 4 * sizeof(unsigned long long), s));
+    a.qs = d_qs;
+    a.qstart = d_qstart;
+    a.nq = nqs;
+    a.ticket_ctr = d_ctr;
+    a.slots = nullptr;
+    kc_run_cfg cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    u64 blocks = 1;
+    int wpb = 1;
+    size_t smem = 0;
+    kc_status st = geometry(branch_kernel<W, MODE>, a.warp_bytes, qstart[nqs], &cfg, &blocks, &wpb, &smem);
+    if (st != KC_OK) return st;
+    branch_kernel<W, MODE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
+    kc_note_launch();
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}
+
+template <int MODE>
+kc_status launch_fixed(int W, const Args &a, const QDesc *qs, u32 nqs, cudaStream_t s, QDesc *d_qs, u64 *d_qstart,
+                       unsigned long long *d_ctr) {
+    switch (W) {
+        case 1: return launch_class_fixed<1, MODE>(a, qs, nqs, s, d_qs, d_qstart, d_ctr);
+        case 2: return launch_class_fixed<2, MODE>(a, qs, nqs, s, d_qs, d_qstart, d_ctr);
+        case 4: return launch_class_fixed<4, MODE>(a, qs, nqs, s, d_qs, d_qstart, d_ctr);
+        case 8: return launch_class_fixed<8, MODE>(a, qs, nqs, s, d_qs, d_qstart, d_ctr);
+        case 16: return launch_class_fixed<16, MODE>(a, qs, nqs, s, d_qs, d_qstart, d_ctr);
+        case 32: return launch_class_fixed<32, MODE>(a, qs, nqs, s, d_qs, d_qstart, d_ctr);
+    }
+    return KC_ERR_UNSUPPORTED;
+}
+}  // namespace
+
+kc_status kc_fill_binom(u128 *table, cudaStream_t s) {
+    binom_kernel<<<1, 64, 0, s>>>(table);
+    kc_note_launch();
+    KC_CUDA(cudaGetLastError());
+    KC_CUDA(cudaStreamSynchronize(s));
+    return KC_OK;
+}
+
+u64 kc_scratch_bytes_for(u32 nq) {
+    return align256(sizeof(kc_dev_acc) * (u64)nq) + align256(sizeof(QDesc) * (u64)nq) +
+           align256(sizeof(u64) * ((u64)nq + 1)) + align256(4 * sizeof(unsigned long long));
+}
+
+kc_status kc_run_queries_in_scratch(const kc_query *qv, u32 nq, u32 t_max, u32 flags, cudaStream_t s,
+                                    unsigned char *d_scratch, u64 scratch_bytes, const u128 *d_binom,
+                                    kc_dev_acc *h_acc) {
+    if (nq == 0) return KC_OK;
+    if (nq > kNoallocMaxQ || kc_scratch_bytes_for(nq) > scratch_bytes) return KC_ERR_INVALID_ARG;
+    unsigned char *p = d_scratch;
+    kc_dev_acc *d_acc = (kc_dev_acc *)p;
+    p += align256(sizeof(kc_dev_acc) * (u64)nq);
+    QDesc *d_qs = (QDesc *)p;
+    p += align256(sizeof(QDesc) * (u64)nq);
+    u64 *d_qstart = (u64 *)p;
+    p += align256(sizeof(u64) * ((u64)nq + 1));
+    unsigned long long *d_ctr = (unsigned long long *)p;
+    // the scratch keeps the previous call's contents: the accumulators start at zero
+    KC_CUDA(cudaMemsetAsync(d_acc, 0, sizeof(kc_dev_acc) * nq, s));
+    Args a;
+    memset(&a, 0, sizeof(a));
+    a.t_max = t_max;
+    a.flags = flags;
+    a.binom = d_binom;
+    const int mode = (flags & KC_CHECKSUM) ? MODE_CHECKSUM : 0;
+    const int widths[6] = {32, 16, 8, 4, 2, 1};
+    kc_status st = KC_OK;
+    for (int wi = 0; wi < 6 && st == KC_OK; wi++) {
+        const int W = widths[wi];
+        QDesc qs[kNoallocMaxQ];
+        u32 nqs = 0;
+        for (u32 i = 0; i < nq; i++) {
+            const kc_graph *g = qv[i].g;
+            const u32 k = qv[i].k;
+            const u64 tau = g->tau;
+            auto suffix = [&](u64 x) -> u64 { return x > tau ? 0ull : g->h_size_suffix[x]; };
+            u64 s_hi = 32ull * W;
+            u64 s_lo = (W == 1) ? 0ull : 16ull * W + 1;
+            if (s_lo < k - 2) s_lo = k - 2;
+            if (s_lo > s_hi) continue;
+            const u64 b = suffix(s_hi + 1), en = suffix(s_lo);
+            if (en <= b) continue;
+            QDesc &d = qs[nqs++];
+            memset(&d, 0, sizeof(d));
+            d.row_ptr = g->row_ptr; d.col = g->col; d.pos_eid = g->pos_eid; d.pos_round = g->pos_round;
+            d.eu = g->eu; d.ev = g->ev; d.round = g->round; d.vset = g->vset; d.tickets = g->tickets;
+            d.vset_ptr = g->vset_ptr;
+            d.k = k;
+            d.t0 = b;
+            d.nt = en - b;
+            d.acc = d_acc + i;
+        }
+        if (!nqs) continue;
+        st = mode == 0 ? launch_fixed<0>(W, a, qs, nqs, s, d_qs, d_qstart, d_ctr)
+                       : launch_fixed<MODE_CHECKSUM>(W, a, qs, nqs, s, d_qs, d_qstart, d_ctr);
+        // the query table in scratch is rewritten for the next class
+        if (st == KC_OK) KC_CUDA(cudaStreamSynchronize(s));
+    }
+    if (st != KC_OK) return st;
+    KC_CUDA(cudaMemcpyAsync(h_acc, d_acc, sizeof(kc_dev_acc) * nq, cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    return KC_OK;
+}

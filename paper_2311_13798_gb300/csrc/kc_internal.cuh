@@ -111,5 +111,16 @@ kc_status kc_run_queries(const kc_query *q, u32 nq, const kc_run_cfg *cfg, cudaS
 // binomial table on the device (saturating u128), built on first use per device
 kc_status kc_ensure_tables(cudaStream_t s);
 
+// entries of the binomial table: C(n, r) for n < 1025, r < 33
+#define KC_BINOM_ENTRIES (1025 * 33)
+
+// ---- no-allocation count path (kc_noalloc.cu): scratch and table supplied by the caller
+kc_status kc_fill_binom(u128 *table, cudaStream_t s);
+u64 kc_scratch_bytes_for(u32 nq);
+kc_status kc_run_queries_in_scratch(const kc_query *q, u32 nq, u32 t_max, u32 flags, cudaStream_t s,
+                                    unsigned char *d_scratch, u64 scratch_bytes, const u128 *d_binom,
+                                    kc_dev_acc *h_acc);
+void kc_set_last_error_msg(const char *msg);
+
 // ---- small host helpers
 static inline u64 kc_div_up(u64 a, u64 b) { return (a + b - 1) / b; }

@@ -100,6 +100,9 @@ def _load():
             lib.kclique_kernel_rev.argtypes = []
             lib.kclique_int_peak.restype = C.c_int
             lib.kclique_int_peak.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int), vp]
+            lib.kclique_count_batch_noalloc.restype = C.c_int
+            lib.kclique_count_batch_noalloc.argtypes = [C.POINTER(vp), C.POINTER(u32), u32, C.POINTER(KcParams), vp,
+                                                        C.POINTER(KcResult)]
             lib.kclique_count_batch.restype = C.c_int
             lib.kclique_count_batch.argtypes = [C.POINTER(vp), C.POINTER(u32), u32, C.POINTER(KcParams), vp,
                                                 C.POINTER(KcResult)]
@@ -271,3 +274,16 @@ def kclique_launch_count(reset: bool = False) -> int:
 
 def kclique_kernel_rev() -> str:
     return _load().kclique_kernel_rev().decode()
+
+
+def kclique_count_batch_noalloc(graphs: list[Graph], ks, stream=None, **kw) -> list[dict]:
+    """Batched count that allocates no device memory (at most 64 queries per call)."""
+    nq = len(graphs)
+    hs = (C.c_void_p * max(nq, 1))(*[g.handle for g in graphs])
+    kk = (C.c_uint32 * max(nq, 1))(*[int(k) for k in ks])
+    res = (KcResult * max(nq, 1))()
+    p = _params(**kw)
+    st = _load().kclique_count_batch_noalloc(hs, kk, nq, C.byref(p), _stream(stream), res)
+    if st != KC_OK:
+        raise KCliqueError(st, "kclique_count_batch_noalloc")
+    return [_result(res[i], KC_OK) for i in range(nq)]
