@@ -544,6 +544,119 @@ __global__ void retire_frontier_kernel(const u32 *__restrict__ F, u32 nf, uint8_
     if (i < nf) st[F[i]] = 2;
 }
 
+// ------------------------------------------------------------ persistent peel
+// The whole level-synchronous peel in one cooperative launch (all blocks resident),
+// rounds separated by a software grid barrier.  Data written by other blocks inside the
+// launch is read with volatile loads (bypassing the non-coherent L1).
+struct PeelState {
+    u32 ctr[4];        // [0] alive after compaction, [1] frontier size, [2] least support, [3] next frontier
+    unsigned bar[2];   // barrier arrivals, generation
+    unsigned status;   // KC_DEV_ERR_* bits
+    u32 rounds;
+};
+
+// A wait longer than 2^35 SM cycles (~17 s) sets KC_DEV_ERR_TIMEOUT and returns.
+__device__ __forceinline__ void grid_sync(PeelState *ps) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &ps->bar[1];
+        const unsigned gen = *vgen;
+        __threadfence();
+        if (atomicAdd(&ps->bar[0], 1u) == gridDim.x - 1) {
+            atomicExch(&ps->bar[0], 0u);
+            __threadfence();
+            atomicAdd(&ps->bar[1], 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == gen) {
+                if (clock64() - t0 > (1ll << 35)) {
+                    atomicOr(&ps->status, KC_DEV_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ u32 vld(const u32 *p) { return *(const volatile u32 *)p; }
+__device__ __forceinline__ uint8_t vld8(const uint8_t *p) { return *(const volatile uint8_t *)p; }
+
+__global__ void __launch_bounds__(256) peel_persistent_kernel(u64 m, const u64 *__restrict__ inc_ptr,
+                                                              const u64 *__restrict__ inc, u32 *sup, uint8_t *st,
+                                                              u32 *level, u32 *round, u32 *alive, u32 *alive2,
+                                                              u32 *F, u32 *Fn, PeelState *ps) {
+    const u64 tid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 nthr = (u64)gridDim.x * blockDim.x;
+    const u64 warp = tid >> 5, nwarps = nthr >> 5;
+    const int lane = threadIdx.x & 31;
+    u32 lvl = 0, r = 0, nf = 0;
+    u64 nalive = m;
+    for (u64 i = tid; i < m; i += nthr) alive[i] = (u32)i;
+    grid_sync(ps);
+    while (!(*(volatile unsigned *)&ps->status & KC_DEV_ERR_TIMEOUT)) {
+        if (nf == 0) {
+            if (nalive == 0) break;
+            if (tid == 0) { ps->ctr[0] = 0; ps->ctr[2] = 0xFFFFFFFFu; }
+            grid_sync(ps);
+            for (u64 i = tid; i < nalive; i += nthr) {
+                const u32 e = vld(&alive[i]);
+                if (vld8(&st[e]) == 2) continue;
+                alive2[atomicAdd(&ps->ctr[0], 1u)] = e;
+                atomicMin(&ps->ctr[2], vld(&sup[e]));
+            }
+            grid_sync(ps);
+            nalive = vld(&ps->ctr[0]);
+            const u32 minsup = vld(&ps->ctr[2]);
+            u32 *t = alive; alive = alive2; alive2 = t;
+            if (nalive == 0) break;
+            if (minsup > lvl) lvl = minsup;
+            grid_sync(ps);  // all have read ctr[0..2]
+            if (tid == 0) ps->ctr[1] = 0;
+            grid_sync(ps);
+            for (u64 i = tid; i < nalive; i += nthr) {
+                const u32 e = vld(&alive[i]);
+                if (vld(&sup[e]) <= lvl) F[atomicAdd(&ps->ctr[1], 1u)] = e;
+            }
+            grid_sync(ps);
+            nf = vld(&ps->ctr[1]);
+            if (nf == 0) {  // cannot happen: the least support is <= lvl
+                if (tid == 0) atomicOr(&ps->status, KC_DEV_ERR_BOUNDS);
+                break;
+            }
+        }
+        for (u64 i = tid; i < nf; i += nthr) {
+            const u32 e = vld(&F[i]);
+            st[e] = 1;
+            level[e] = lvl;
+            round[e] = r;
+        }
+        if (tid == 0) ps->ctr[3] = 0;
+        grid_sync(ps);
+        for (u64 i = warp; i < nf; i += nwarps) {
+            const u32 e = vld(&F[i]);
+            for (u64 p = inc_ptr[e] + lane; p < inc_ptr[e + 1]; p += 32) {
+                const u64 pr = inc[p];
+                const u32 e1 = (u32)(pr >> 32), e2 = (u32)pr;
+                const uint8_t s1 = vld8(&st[e1]), s2 = vld8(&st[e2]);
+                if (s1 == 2 || s2 == 2) continue;                       // destroyed in an earlier round
+                if ((s1 == 1 && e1 < e) || (s2 == 1 && e2 < e)) continue;  // another frontier edge owns it
+                if (s1 == 0) { u32 old = atomicSub(&sup[e1], 1u); if (old == lvl + 1) Fn[atomicAdd(&ps->ctr[3], 1u)] = e1; }
+                if (s2 == 0) { u32 old = atomicSub(&sup[e2], 1u); if (old == lvl + 1) Fn[atomicAdd(&ps->ctr[3], 1u)] = e2; }
+            }
+        }
+        grid_sync(ps);
+        for (u64 i = tid; i < nf; i += nthr) st[vld(&F[i])] = 2;
+        nf = vld(&ps->ctr[3]);
+        u32 *t = F; F = Fn; Fn = t;
+        r++;
+        grid_sync(ps);  // retired, and everyone has read ctr[3]
+    }
+    if (tid == 0) ps->rounds = r;
+}
+
 // ------------------------------------------------------------ VSet
 __device__ __forceinline__ bool key_less(u32 ra, u32 ea, u32 rb, u32 eb) { return ra < rb || (ra == rb && ea < eb); }
 
@@ -805,10 +918,38 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
         iota_kernel<<<grid_for(m), TPB, 0, s>>>(alive, m);
         kc_note_launch();
     }
-    u64 nalive = m;
+    // one cooperative persistent launch when the device supports it (host-driven rounds otherwise)
+    bool peeled = false;
+    {
+        int dev = 0, coop = 0, nsm = 0, per_sm = 0;
+        KC_CUDA(cudaGetDevice(&dev));
+        KC_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        KC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, peel_persistent_kernel, 256, 0));
+        if (coop && per_sm > 0 && m > 0) {
+            PeelState *ps;
+            KC_TRY(dalloc(&ps, 1, s, &scr));
+            KC_CUDA(cudaMemsetAsync(ps, 0, sizeof(PeelState), s));
+            u32 *lvl_p = g->level, *rnd_p = g->round;
+            const u64 *incp = inc_ptr, *incc = inc;
+            void *kargs[] = {(void *)&m, (void *)&incp, (void *)&incc, (void *)&sup, (void *)&st, (void *)&lvl_p,
+                             (void *)&rnd_p, (void *)&alive, (void *)&alive2, (void *)&F, (void *)&Fn, (void *)&ps};
+            const unsigned grid = (unsigned)std::min<u64>((u64)nsm * per_sm, kc_div_up(m, 256));
+            KC_CUDA(cudaLaunchCooperativeKernel((void *)peel_persistent_kernel, dim3(grid), dim3(256), kargs, 0, s));
+            kc_note_launch();
+            PeelState h;
+            KC_CUDA(cudaMemcpyAsync(&h, ps, sizeof(PeelState), cudaMemcpyDeviceToHost, s));
+            KC_CUDA(cudaStreamSynchronize(s));
+            if (h.status & KC_DEV_ERR_TIMEOUT) return KC_ERR_TIMEOUT;
+            if (h.status) return KC_ERR_CUDA;
+            g->rounds = h.rounds;
+            peeled = true;
+        }
+    }
+    u64 nalive = peeled ? 0 : m;
     u32 lvl = 0, r = 0;
     u32 nf = 0;
-    while (true) {
+    while (!peeled) {
         if (nf == 0) {
             if (nalive == 0) break;
             KC_CUDA(cudaMemsetAsync(ctr, 0, sizeof(u32) * 2, s));
@@ -842,7 +983,7 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
         std::swap(F, Fn);
         r++;
     }
-    g->rounds = r;
+    if (!peeled) g->rounds = r;
 
     // ---- A4: VSet
     u32 *vcnt;

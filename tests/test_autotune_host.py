@@ -1,0 +1,36 @@
+"""Autotuner selection and caching logic on CPU (timings injected)."""
+import json
+
+from paper_2311_13798_gb300.autotune import Autotuner, shape_key
+
+
+def test_picks_fastest_and_caches(tmp_path):
+    calls = []
+
+    def timer(h, k, p):
+        calls.append(dict(p))
+        return 10.0 + (p["split_min"] == 128) * -5.0 + (p["t_max"] == 1) * 3.0
+
+    path = str(tmp_path / "tune.json")
+    t = Autotuner(cache_path=path, timer=timer, device_name="GB300")
+    info = {"m": 10_000_000, "tau": 246}
+    best = t.tune(object(), 7, info)
+    assert best == {"split_min": 128, "t_max": 2, "blocks": 0}
+    n = len(calls)
+    assert t.tune(object(), 7, info) == best and len(calls) == n  # cached, not re-measured
+    d = json.load(open(path))
+    assert shape_key(info, 7, "GB300") in d
+    # a new tuner reads the cache from disk
+    t2 = Autotuner(cache_path=path, timer=lambda *a: 1 / 0, device_name="GB300")
+    assert t2.tune(object(), 7, info) == best
+
+
+def test_small_k_does_not_sweep_split():
+    seen = set()
+
+    def timer(h, k, p):
+        seen.add(p["split_min"])
+        return 1.0
+
+    Autotuner(timer=timer, device_name="x").tune(object(), 5, {"m": 100, "tau": 3})
+    assert len(seen) == 1
