@@ -50,6 +50,10 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", choices=["power_law", "batch", "serve"], default="power_law",
+                    help="power_law: the default bench line; batch / serve: the batching and serving "
+                         "measurements (separate JSON lines)")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
     return ap.parse_args(argv)
 
 
@@ -188,10 +192,164 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
+def run_batch(args):
+    """Many small uneven graphs, each with its own k: one kclique_count_batch call
+    (one persistent launch per width class) against one kclique_count per graph."""
+    import numpy as np
+    import torch
+
+    from paper_2311_13798_gb300 import kclique as K
+    from synth import graphs as G
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    specs = G.batch_specs(count=args.batch_graphs, seed=0)
+    graphs = [G.batch_graph(sp) for sp in specs]
+    gen_s = time.perf_counter() - t0
+    handles = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in graphs:
+        rp = torch.from_numpy(g.row_ptr.astype(np.int32)).cuda()
+        col = torch.from_numpy(g.col.astype(np.int32)).cuda()
+        handles.append(K.kclique_prepare(rp, col, g.n))
+    torch.cuda.synchronize()
+    prep_s = time.perf_counter() - t0
+    ks = [sp["k"] for sp in specs]
+    for _ in range(args.warmup):
+        K.kclique_count_batch(handles, ks)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res_b = K.kclique_count_batch(handles, ks)
+    torch.cuda.synchronize()
+    batch_s = (time.perf_counter() - t0) / args.steps
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res_s = [K.kclique_count(h, k) for h, k in zip(handles, ks)]
+    torch.cuda.synchronize()
+    single_s = (time.perf_counter() - t0) / args.steps
+    assert [r["count"] for r in res_b] == [r["count"] for r in res_s]
+    cliques = sum(r["count"] for r in res_b)
+    line = {"metric": "batched k-clique queries/s", "workload": "batch", "value": len(ks) / batch_s,
+            "unit": "queries/s", "one_query_per_launch": len(ks) / single_s, "speedup": single_s / batch_s,
+            "k-cliques/s": cliques / batch_s, "n_graphs": len(ks), "edges": int(sum(g.m for g in graphs)),
+            "cliques": str(cliques), "ms_batch": batch_s * 1e3, "ms_one_per_launch": single_s * 1e3,
+            "prepare_s": prep_s, "generate_s": gen_s, "steps": args.steps, "warmup": args.warmup,
+            "config": {"graphs": "G(n,p), n~U{64..4096}, avg degree U[8,64], 1-4 planted cliques U{8..24}, "
+                                 "k~U{3..10}, seed 0"}}
+    print(json.dumps(line), flush=True)
+
+
+def serve_trace(n_arrivals: int, rate: float, seed: int = 0):
+    """Poisson arrivals: 70% count/list queries (50/50) on 8 resident graphs with k ~ U{4..10},
+    30% uploads of a small block graph (4 blocks x 250, one of them an exact 2-plex)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n_arrivals))
+    kinds = rng.choice(["count", "list", "upload"], size=n_arrivals, p=[0.35, 0.35, 0.30])
+    gids = rng.integers(0, 8, size=n_arrivals)
+    ks = rng.integers(4, 11, size=n_arrivals)
+    return [(float(t[i]), str(kinds[i]), int(gids[i]), int(ks[i]), i) for i in range(n_arrivals)]
+
+
+def run_serve(args):
+    """Continuous-batching server on a Poisson trace vs the same trace run FIFO with one
+    query per launch; p50/p99 latency from arrival to completion."""
+    import numpy as np
+    import torch
+
+    from paper_2311_13798_gb300 import kclique as K
+    from paper_2311_13798_gb300.serve import CudaBackend, KCliqueServer, Request
+    from synth import graphs as G
+    torch.cuda.set_device(0)
+    base = [G.config1(seed=sd) for sd in range(4)] + \
+           [G.chung_lu(n=100_000, w_max=2000.0, i0=40.0, planted=20, seed=sd) for sd in range(4)]
+    n_arr = max(200, args.steps * 1000)
+    trace = serve_trace(n_arr, 2000.0, seed=0)
+    uploads = {}
+    for (t, kind, gid, k, i) in trace:
+        if kind == "upload":
+            g, _ = G.sbm_2plex(blocks=4, block_size=250, p_in=0.9, p_out=1e-3, two_plex_blocks=1, seed=1000 + i)
+            uploads[i] = g
+    cap = 1024
+
+    def replay_server():
+        srv = KCliqueServer(CudaBackend(), hbm_budget_bytes=120 << 30)
+        for j, g in enumerate(base):
+            srv.register(f"g{j}", g.row_ptr, g.col, g.n)
+        torch.cuda.synchronize()
+        futs = []
+        t0 = time.perf_counter()
+        for (t, kind, gid, k, i) in trace:
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            if kind == "upload":
+                g = uploads[i]
+                req = Request("upload", f"u{i}", csr=(g.row_ptr, g.col, g.n), t_arrival=t0 + t)
+            else:
+                req = Request(kind, f"g{gid}", k=k, cap=cap, t_arrival=t0 + t)
+            futs.append(srv.submit(req))
+        res = [f.result(timeout=3600) for f in futs]
+        srv.close()
+        return srv.stats(), res
+
+    def replay_fifo():
+        hs = []
+        for g in base:
+            hs.append(K.kclique_prepare(g.row_ptr, g.col, g.n))
+        out = torch.empty((cap, 10), dtype=torch.int32, device="cuda")
+        lat, res = [], []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (t, kind, gid, k, i) in trace:
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            if kind == "upload":
+                g = uploads[i]
+                K.kclique_prepare(g.row_ptr, g.col, g.n).release()
+                res.append(None)
+            elif kind == "count":
+                r = K.kclique_count(hs[gid], k, flags=K.KC_CHECKSUM)
+                res.append((r["count"], r["checksum"]))
+                lat.append(time.perf_counter() - t0 - t)
+            else:
+                o = torch.empty((cap, k), dtype=torch.int32, device="cuda")
+                r = K.kclique_list(hs[gid], k, o)
+                res.append((r["count"], r["checksum"]))
+                lat.append(time.perf_counter() - t0 - t)
+        span = time.perf_counter() - t0
+        lat.sort()
+        nq = len(lat)
+        return {"p50_s": lat[nq // 2], "p99_s": lat[min(nq - 1, int(0.99 * (nq - 1)))], "throughput_qps": nq / span,
+                "queries": nq}, res
+
+    st_srv, res_srv = replay_server()
+    st_fifo, res_fifo = replay_fifo()
+    same = all(a is None or r.kind == "upload" or (r.count, r.checksum) == a
+               for r, a in zip(res_srv, res_fifo))
+    line = {"metric": "served k-clique queries/s (continuous batching)", "workload": "serve",
+            "value": st_srv["throughput_qps"], "unit": "queries/s", "p50_s": st_srv["p50_s"],
+            "p99_s": st_srv["p99_s"], "batches": st_srv["batches"], "mean_batch": st_srv["mean_batch"],
+            "rejected": st_srv["rejected"], "one_query_per_launch": st_fifo,
+            "speedup": st_srv["throughput_qps"] / st_fifo["throughput_qps"], "results_identical": same,
+            "config": {"arrivals": n_arr, "rate_qps": 2000, "resident": "4 x G(2000,0.01) seeds 0-3 + "
+                       "4 x Chung-Lu n=1e5 wmax=2000 seeds 0-3", "k": "U{4..10}", "mix": "35% count, 35% list "
+                       "(cap 1024 rows), 30% upload of 4x250 SBM with one 2-plex block", "hbm_budget_GB": 120}}
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     import numpy as np
     import torch

@@ -972,8 +972,9 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                 }
             } else {
                 bool closed = false;
-                if (!SUM && l2 == 3 && has && cc >= 3 && use_et && cc <= 64) {
-                    // small l = 3 child: the t-plex test and the Alg. 6 count in this lane
+                if (!SUM && l2 == 3 && has && cc >= 3 && use_et) {
+                    // l = 3 child: the t-plex test and the Alg. 6 count in this lane (a lane
+                    // leaves the test at its first vertex of too small degree)
                     const int tmax = (int)a.t_max;
                     const int w0 = cv >> 5;  // the child's set has no bits below v's word
                     int nuni = 0;
