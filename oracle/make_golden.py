@@ -8,6 +8,7 @@ so a long run can be stopped and resumed.
 
     python oracle/make_golden.py c1            # seconds
     python oracle/make_golden.py c2 5 7 9      # minutes to hours
+    python oracle/make_golden.py c2edges 9     # per-edge sub-branch values at k = 9
     python oracle/make_golden.py c3blocks 6 7  # per-block values for the SBM workload
 """
 import json
@@ -76,6 +77,25 @@ def main(argv):
         cg = _graph_entry("c2", g)
         for k in ks or [5, 7, 9]:
             _count_entry("c2", cg, k, threads)
+    elif what == "c2edges":
+        # per-edge sub-branch counts (Eq. 2) for a deterministic sample of edges: the 8
+        # largest VSets (ties by edge id) and 40 random edges with |VSet| >= k-2
+        g = G.chung_lu()
+        cg = O.CleanGraph.of(g)
+        lvl, rnd, _ = O.truss_peel(cg)
+        vs = O.vset_sizes(cg, rnd).astype(np.int64)
+        for k in ks or [9]:
+            order = np.lexsort((np.arange(vs.size), -vs))
+            heavy = order[:8]
+            rng = np.random.default_rng(k)
+            cand = np.nonzero(vs >= k - 2)[0]
+            rand = np.sort(rng.choice(cand, size=min(40, cand.size), replace=False))
+            edges = np.unique(np.concatenate([heavy, rand]))
+            t = time.time()
+            cnt, cs = O.edge_counts(cg, k, rnd, edges, threads=threads)
+            _store(f"c2/edges_k{k}", {"edges": edges.tolist(), "vset": vs[edges].tolist(),
+                                      "count": [str(c) for c in cnt], "checksum": [str(c) for c in cs],
+                                      "wall_s": round(time.time() - t, 2), "threads": threads})
     elif what == "c3blocks":
         g, info = G.sbm_2plex()
         _store("c3/graph", {"fingerprint": g.fingerprint(), "n": g.n, "m": g.m,

@@ -164,6 +164,9 @@ struct Lay {
     u32 *childUV;    // [D][32]
     u32 *path;       // [2D+4]
     uint16_t *bu, *bv;  // [32]
+    uint8_t *bs;        // [32] ring slot of each batch entry's u (plex pre-check)
+    u32 *Bm, *M1;       // [D][4][W] per-u masks of the last 4 u's at each depth (plex pre-check)
+    int *rn;            // [D] u's entered into the ring so far
     u32 *tmpW;       // [W]
     u32 *tmpW2;      // [W]
 };
@@ -191,6 +194,9 @@ __host__ __device__ u32 lay_bytes(u32 D, bool sum) {
     b += align16<W>(4u * D * 32);      // childUV
     b += align16<W>(4u * (2 * D + 4)); // path
     b += align16<W>(2u * 64);          // bu, bv
+    b += align16<W>(32u);              // bs
+    b += align16<W>(2u * 4u * D * 4 * W);  // Bm, M1
+    b += align16<W>(4u * D);           // rn
     b += align16<W>(8u * W);           // tmpW, tmpW2
     return b;
 }
@@ -217,6 +223,9 @@ __device__ Lay make_lay(unsigned char *p, u32 D, bool sum) {
     L.childUV = (u32 *)(p + o); o += align16<W>(4u * D * 32);
     L.path = (u32 *)(p + o); o += align16<W>(4u * (2 * D + 4));
     L.bu = (uint16_t *)(p + o); L.bv = L.bu + 32; o += align16<W>(2u * 64);
+    L.bs = (uint8_t *)(p + o); o += align16<W>(32u);
+    L.Bm = (u32 *)(p + o); L.M1 = L.Bm + D * 4 * W; o += align16<W>(2u * 4u * D * 4 * W);
+    L.rn = (int *)(p + o); o += align16<W>(4u * D);
     L.tmpW = (u32 *)(p + o); L.tmpW2 = L.tmpW + W; o += align16<W>(8u * W);
     return L;
 }
@@ -355,7 +364,9 @@ __device__ void extract(const Lay &L, const QDesc &q, int s, u32 e, u32 re, int 
         }
         const u32 dx = xe - xb;
         const int rem = s - 1 - i;
-        if (dx <= 4u * (u32)rem) {
+        // scan the row (coalesced global loads, binary search in shared vid) unless it is
+        // much longer than the candidates; dependent global binary searches are latency bound
+        if (dx <= 32u * (u32)rem) {
             for (u32 p = xb + lane; p < xe; p += 32) {
                 acc.pairs++;
                 u32 y = q.col[p];
@@ -584,7 +595,7 @@ __device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l
     return true;
 }
 
-// ---------------------------------------------------------------- l = 3 frames (count only)
+// ---------------------------------------------------------------- l = 3 frames
 // The 3-cliques of g[C]: a lane per vertex x of C computes deg(x) in C; then, whichever
 // side is sparser, either the triangles directly,
 //     sum_x sum_{y in N(x) & C, y > x} |N(x) & N(y) & C & {> y}|,
@@ -592,8 +603,31 @@ __device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l
 //     C(c,3) - |M| (c-2) + sum_x C(dbar(x), 2) - T(complement),
 // with dbar the missing degree and T(complement) the triples with no edge.  A
 // clique or 2-plex (Sec. 5 test, t <= t_max) is closed by the Alg. 6 count instead.
-template <int W>
-__device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, int tmax, bool use_et, int ws) {
+// SUM: also the checksum P * sum over triangles of z_a z_b z_c -- for plexes the x^3
+// coefficient of prod (1 + c x) (c = z_f for a universal vertex, z_a + z_b per missing
+// pair), for the complement side the same identity with weights:
+//     e3(z_C) - sum_{ab in M} z_a z_b (Z - z_a - z_b) + sum_x z_x e2(z of non-nbrs of x) - T_z.
+
+// product of two truncated polynomials (1 + a1 x + a2 x^2 + a3 x^3)(1 + b1 x + ...)
+__device__ __forceinline__ void poly3_mul(u64 &a1, u64 &a2, u64 &a3, u64 b1, u64 b2, u64 b3) {
+    const u64 c3 = a3 + b3 + a1 * b2 + a2 * b1;
+    const u64 c2 = a2 + b2 + a1 * b1;
+    a1 += b1;
+    a2 = c2;
+    a3 = c3;
+}
+
+__device__ __forceinline__ void poly3_warp_product(u64 &p1, u64 &p2, u64 &p3) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 b1 = __shfl_xor_sync(0xffffffffu, p1, o);
+        const u64 b2 = __shfl_xor_sync(0xffffffffu, p2, o);
+        const u64 b3 = __shfl_xor_sync(0xffffffffu, p3, o);
+        poly3_mul(p1, p2, p3, b1, b2, b3);
+    }
+}
+
+template <int W, bool SUM>
+__device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, int tmax, bool use_et, int ws, u64 P) {
     u32 cw[W];
     int cnt = 0;
 #pragma unroll
@@ -604,6 +638,7 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
     if (cnt < 3) return;
     u64 sumdeg = 0, sc2 = 0;
     int mind = cnt, nuni = 0;
+    u64 Z = 0, q1 = 0, q2 = 0, q3 = 0;  // SUM: sum of keys, lane's part of prod (1 + z x)
     for (int base = 0; base < cnt; base += 32) {
         const int i = base + lane;
         if (i < cnt) {
@@ -612,17 +647,24 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
 #pragma unroll
             for (int w = 0; w < W; w++) d += __popc(L.A[x * W + w] & cw[w]);
             L.aux2[i] = (uint16_t)x;
+            L.aux[i] = (uint16_t)d;
             const int db = cnt - 1 - d;
             sumdeg += (u64)d;
             sc2 += (u64)db * (u64)(db - 1) / 2;
             mind = min(mind, d);
             nuni += (db == 0);
             acc.ops += 2u * (u32)ws;
+            if (SUM) {
+                const u64 z = L.z[x];
+                Z += z;
+                poly3_mul(q1, q2, q3, z, 0ull, 0ull);
+            }
         }
     }
     __syncwarp();
     sumdeg = warp_sum_u64(sumdeg);
     sc2 = warp_sum_u64(sc2);
+    if (SUM) Z = warp_sum_u64(Z);  // the key sum over all of C
     mind = (int)__reduce_min_sync(0xffffffffu, (unsigned)mind);
     nuni = (int)__reduce_add_sync(0xffffffffu, (unsigned)nuni);
     const u64 c = (u64)cnt;
@@ -638,11 +680,33 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
             add = f * (f - 1) * (f - 2) / 6 + (f * (f - 1) / 2) * pp * 2 + f * (pp * (pp - 1) / 2) * 4 +
                   (pp * (pp - 1) * (pp - 2) / 6) * 8;
         }
+        if (SUM) {
+            u64 p1 = 0, p2 = 0, p3 = 0;
+            for (int base = 0; base < cnt; base += 32) {
+                const int i = base + lane;
+                if (i < cnt) {
+                    const int x = L.aux2[i];
+                    if (L.aux[i] == cnt - 1) {
+                        poly3_mul(p1, p2, p3, L.z[x], 0ull, 0ull);
+                    } else {  // its one missing partner y; the pair's factor once, from min(x, y)
+                        int y = -1;
+#pragma unroll
+                        for (int w = 0; w < W; w++) {
+                            const u32 nb = cw[w] & ~L.A[x * W + w] & ~((w == (x >> 5)) ? (1u << (x & 31)) : 0u);
+                            if (y < 0 && nb) y = w * 32 + __ffs(nb) - 1;
+                        }
+                        if (y > x) poly3_mul(p1, p2, p3, L.z[x] + L.z[y], 0ull, 0ull);
+                    }
+                }
+            }
+            poly3_warp_product(p1, p2, p3);
+            if (lane == 0) acc.csum += P * p3;
+        }
         if (lane == 0) { acc.leaf += add; acc.et++; }
         return;
     }
     const bool comp = M < E;
-    u64 t = 0;
+    u64 t = 0, zsum = 0;
     for (int base = 0; base < cnt; base += 32) {
         const int i = base + lane;
         if (i < cnt) {
@@ -653,22 +717,59 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
                 const u32 ax = comp ? ~L.A[x * W + w] : L.A[x * W + w];
                 row[w] = ax & cw[w] & gt_mask(x, w);
             }
-#pragma unroll
+            const u64 zx = SUM ? L.z[x] : 0ull;
+            if (SUM && comp) {
+                // z_x e2(keys of all non-neighbours of x in C)
+                u64 f1 = 0, f2 = 0;
+#pragma unroll (W <= 8 ? W : 1)
+                for (int w = 0; w < W; w++) {
+                    u32 nb = cw[w] & ~L.A[x * W + w] & ~((w == (x >> 5)) ? (1u << (x & 31)) : 0u);
+                    while (nb) {
+                        const u64 z = L.z[w * 32 + __ffs(nb) - 1];
+                        nb &= nb - 1;
+                        f2 += f1 * z;
+                        f1 += z;
+                    }
+                }
+                zsum += zx * f2;
+            }
+#pragma unroll (W <= 8 ? W : 1)
             for (int w = 0; w < W; w++) {
                 u32 bits = row[w];
                 while (bits) {
                     const int y = w * 32 + __ffs(bits) - 1;
                     bits &= bits - 1;
                     int tc = 0;
+                    u64 zw = 0;
 #pragma unroll
                     for (int w2 = 0; w2 < W; w2++) {
                         const u32 ay = comp ? ~L.A[y * W + w2] : L.A[y * W + w2];
-                        tc += __popc(row[w2] & ay & gt_mask(y, w2));
+                        u32 tb = row[w2] & ay & gt_mask(y, w2);
+                        tc += __popc(tb);
+                        if (SUM) {
+                            while (tb) { zw += L.z[w2 * 32 + __ffs(tb) - 1]; tb &= tb - 1; }
+                        }
                     }
                     t += (u64)tc;
+                    if (SUM) {
+                        const u64 zy = L.z[y];
+                        if (comp) zsum -= zx * zy * (Z - zx - zy) + zx * zy * zw;  // missing pair, complement triangles
+                        else zsum += zx * zy * zw;
+                    }
                     acc.ops += 3u * (u32)(ws - (y >> 5));
                 }
             }
+        }
+    }
+    if (SUM) {
+        // warp-wide: e3 of all keys (complement side), the lanes' weighted terms
+        if (comp) {
+            u64 p1 = q1, p2 = q2, p3 = q3;
+            poly3_warp_product(p1, p2, p3);
+            zsum = warp_sum_u64(zsum);
+            if (lane == 0) acc.csum += P * (p3 + zsum);
+        } else {
+            acc.csum += P * zsum;
         }
     }
     if (!comp) {
@@ -779,7 +880,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
     const u32 k = q.k;
     long long tsec = 0;
     if (lane < W) L.C0[lane] = lt_mask(s, lane);
-    if (lane == 0) { L.cur[0] = u_lo - 1; L.slot[0] = 0; }
+    if (lane == 0) { L.cur[0] = u_lo - 1; L.slot[0] = 0; L.rn[0] = 0; }
     if (lane < W) L.V[lane] = 0;
     __syncwarp();
     int d = 0;
@@ -791,19 +892,19 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
         const u64 P = SUM ? (d == 0 ? P0 : L.childP[d * 32 + L.slot[d]]) : 0ull;
         if (phase == 0) {
             if (lane == 0) acc.nodes++;
-            if (!SUM && l == 3) {
+            if (LIST) full = *(volatile unsigned long long *)&q.acc->written >= a.cap;
+            if (l == 3 && (!LIST || full)) {
                 KC_SEC_BEGIN();
-                frame_l3_count<W>(L, C, lane, acc, (int)a.t_max, use_et, Ws);
+                frame_l3_count<W, SUM>(L, C, lane, acc, (int)a.t_max, use_et, Ws, P);
                 KC_SEC_END(3);
                 phase = 3;
                 continue;
             }
-            if (LIST) full = *(volatile unsigned long long *)&q.acc->written >= a.cap;
             KC_SEC_BEGIN();
             const bool closed = early_terminate<W, MODE>(L, a, C, l, P, lane, acc, use_et && (!LIST || full), Ws);
             KC_SEC_END(2);
             if (closed) { phase = 3; continue; }
-            if (lane == 0) L.cur[d] = d == 0 ? u_lo - 1 : -1;
+            if (lane == 0) { L.cur[d] = d == 0 ? u_lo - 1 : -1; L.rn[d] = 0; }
             if (lane < W) L.V[d * W + lane] = 0;
             __syncwarp();
             phase = 1;
@@ -818,18 +919,57 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
             int nb = 0;
             u32 *V = L.V + d * W;
             int u = L.cur[d];
+            // plex pre-check for l = 3 children (count mode): masks of the current u
+            const bool pre = !SUM && l == 5 && use_et;
+            int nuniq = 0;  // distinct u's in this batch (at most 4: the ring)
+            if (pre) {
+                u32 vw0 = lane < W ? V[lane] : 0u;
+                nuniq = __any_sync(0xffffffffu, vw0 != 0) ? 1 : 0;
+            }
             while (nb < 32) {
                 u32 vw = lane < W ? V[lane] : 0u;
                 int c = __popc(vw);
                 int tot = __reduce_add_sync(0xffffffffu, (unsigned)c);
                 if (tot == 0) {
                     if (u == -2) break;  // generator exhausted
+                    if (pre && nuniq == 4) break;  // ring full: evaluate this batch first
                     int nu = warp_first_from<W>(C, u + 1, lane);
                     if (nu < 0 || nu >= limu) { u = -2; break; }
                     u = nu;
                     u32 nv = 0;
                     if (lane < W) nv = L.A[u * W + lane] & C[lane] & gt_mask(u, lane) & lt_mask(limv, lane);
                     if (lane < W) V[lane] = nv;
+                    if (pre && __any_sync(0xffffffffu, nv != 0)) {
+                        // over Cu = C & N(u) & {> u}: B = vertices with >= t_max non-neighbours
+                        // in Cu, M1 = vertices with >= 1; every child set of u lies inside Cu
+                        const int slot = L.rn[d] & 3;
+                        u32 cu[W];
+                        int ncu = 0;
+#pragma unroll
+                        for (int w = 0; w < W; w++) {
+                            cu[w] = C[w] & L.A[u * W + w] & gt_mask(u, w);
+                            ncu += __popc(cu[w]);
+                        }
+                        u32 *Bm = L.Bm + (d * 4 + slot) * W, *M1 = L.M1 + (d * 4 + slot) * W;
+                        if (lane < W) { Bm[lane] = 0; M1[lane] = 0; }
+                        __syncwarp();
+                        const int tm = (int)a.t_max;
+                        for (int base = 0; base < ncu; base += 32) {
+                            const int i = base + lane;
+                            if (i < ncu) {
+                                const int x = select_bit<W>(cu, i);
+                                int md = -1;  // x itself is not in N(x)
+#pragma unroll
+                                for (int w = 0; w < W; w++) md += __popc(cu[w] & ~L.A[x * W + w]);
+                                if (md >= tm) atomicOr(&Bm[x >> 5], 1u << (x & 31));
+                                if (md >= 1) atomicOr(&M1[x >> 5], 1u << (x & 31));
+                                acc.ops += 2u * (u32)Ws;
+                            }
+                        }
+                        __syncwarp();
+                        if (lane == 0) L.rn[d] = L.rn[d] + 1;
+                        nuniq++;
+                    }
                     __syncwarp();
                     continue;
                 }
@@ -841,11 +981,13 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                 off -= c;
                 int room = 32 - nb;
                 int take = max(0, min(c, room - off));
+                const uint8_t rs = pre ? (uint8_t)((L.rn[d] - 1) & 3) : (uint8_t)0;
                 for (int i = 0; i < take; i++) {
                     int b = __ffs(vw) - 1;
                     vw &= vw - 1;
                     L.bu[nb + off + i] = (uint16_t)u;
                     L.bv[nb + off + i] = (uint16_t)(lane * 32 + b);
+                    L.bs[nb + off + i] = rs;
                 }
                 if (lane < W) V[lane] = vw;
                 nb += min(tot, room);
@@ -876,7 +1018,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                 acc.leaf += (u64)cc;
                 if (SUM && cc) {
                     u64 zs = 0;
-#pragma unroll
+#pragma unroll (W <= 8 ? W : 1)
                     for (int w = 0; w < W; w++) {
                         u32 x = cw[w];
                         while (x) { int b = __ffs(x) - 1; x &= x - 1; zs += L.z[w * 32 + b]; }
@@ -900,7 +1042,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                     ids[np] = L.vid[cu];
                     ids[np + 1] = L.vid[cv];
                     int idx = 0;
-#pragma unroll
+#pragma unroll (W <= 8 ? W : 1)
                     for (int w = 0; w < W; w++) {
                         u32 x = cw[w];
                         while (x) {
@@ -917,7 +1059,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
             } else if (l2 == 2) {
                 if (cc >= 2) {
                     u64 ec = 0, zs = 0;
-#pragma unroll
+#pragma unroll (W <= 8 ? W : 1)
                     for (int w = 0; w < W; w++) {
                         u32 x = cw[w];
                         while (x) {
@@ -973,13 +1115,53 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
             } else {
                 bool closed = false;
                 if (!SUM && l2 == 3 && has && cc >= 3 && use_et) {
+                    // pre-check against the masks of this child's u: no vertex of C' has
+                    // t_max non-neighbours even in the larger set Cu => C' is a t-plex
+                    const int slot = L.bs[lane];
+                    const u32 *Bm = L.Bm + (d * 4 + slot) * W, *M1 = L.M1 + (d * 4 + slot) * W;
+                    bool bad = false, any1 = false;
+#pragma unroll
+                    for (int w = 0; w < W; w++) {
+                        bad |= (cw[w] & Bm[w]) != 0u;
+                        any1 |= (cw[w] & M1[w]) != 0u;
+                    }
+                    if (!bad) {
+                        const u64 c = (u64)cc;
+                        u64 nonuni = 0;
+                        if (any1) {  // count the vertices with a non-neighbour inside C'
+#pragma unroll (W <= 8 ? W : 1)
+                            for (int w = 0; w < W; w++) {
+                                u32 bits = cw[w] & M1[w];
+                                while (bits) {
+                                    const int x = w * 32 + __ffs(bits) - 1;
+                                    bits &= bits - 1;
+                                    bool nb = false;
+#pragma unroll
+                                    for (int w2 = 0; w2 < W; w2++)
+                                        nb |= (cw[w2] & ~L.A[x * W + w2] & ~((w2 == (x >> 5)) ? (1u << (x & 31)) : 0u)) != 0u;
+                                    nonuni += nb;
+                                }
+                            }
+                        }
+                        const u64 f = c - nonuni, pp = nonuni / 2;
+                        acc.leaf += f * (f - 1) * (f - 2) / 6 + (f * (f - 1) / 2) * pp * 2 + f * (pp * (pp - 1) / 2) * 4 +
+                                    (pp * (pp - 1) * (pp - 2) / 6) * 8;
+                        acc.ops += 2u * (u32)(Ws - (cv >> 5));
+                        acc.et++;
+                        acc.nodes++;
+                        closed = true;
+                    }
+                }
+                if (!closed && l2 == 3 && has && cc >= 3 && use_et && (!LIST || full)) {
                     // l = 3 child: the t-plex test and the Alg. 6 count in this lane (a lane
-                    // leaves the test at its first vertex of too small degree)
+                    // leaves the test at its first vertex of too small degree); SUM: the x^3
+                    // coefficient of prod (1 + c x), c = z_f (universal) or z_a + z_b (pair)
                     const int tmax = (int)a.t_max;
                     const int w0 = cv >> 5;  // the child's set has no bits below v's word
                     int nuni = 0;
                     bool plex = true;
-#pragma unroll
+                    u64 p1 = 0, p2 = 0, p3 = 0;
+#pragma unroll (W <= 8 ? W : 1)
                     for (int w = 0; w < W; w++) {
                         u32 bits = plex ? cw[w] : 0u;
                         while (bits) {
@@ -991,6 +1173,20 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                                 if (w2 >= w0) dg += __popc(L.A[x * W + w2] & cw[w2]);
                             if (dg < cc - tmax) { plex = false; bits = 0; }
                             nuni += (dg == cc - 1);
+                            if (SUM && plex) {
+                                if (dg == cc - 1) {
+                                    poly3_mul(p1, p2, p3, L.z[x], 0ull, 0ull);
+                                } else {
+                                    int y = -1;
+#pragma unroll
+                                    for (int w2 = 0; w2 < W; w2++) {
+                                        const u32 nb = (w2 >= w0) ? (cw[w2] & ~L.A[x * W + w2] &
+                                                                     ~((w2 == (x >> 5)) ? (1u << (x & 31)) : 0u)) : 0u;
+                                        if (y < 0 && nb) y = w2 * 32 + __ffs(nb) - 1;
+                                    }
+                                    if (y > x) poly3_mul(p1, p2, p3, L.z[x] + L.z[y], 0ull, 0ull);
+                                }
+                            }
                         }
                     }
                     acc.ops += 2u * (u32)(Ws - w0) * (u32)cc;
@@ -998,6 +1194,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                         const u64 c = (u64)cc, f = (u64)nuni, pp = (c - f) / 2;
                         acc.leaf += f * (f - 1) * (f - 2) / 6 + (f * (f - 1) / 2) * pp * 2 + f * (pp * (pp - 1) / 2) * 4 +
                                     (pp * (pp - 1) * (pp - 2) / 6) * 8;
+                        if (SUM) acc.csum += Pc * p3;
                         acc.et++;
                         acc.nodes++;
                         closed = true;
@@ -1134,7 +1331,7 @@ branch_kernel(Args a) {
                 for (int i = lane; i < s; i += 32) {
                     u32 c = 0;
                     u64 zs = 0;
-#pragma unroll
+#pragma unroll (W <= 8 ? W : 1)
                     for (int w = 0; w < W; w++) {
                         u32 x = L.A[i * W + w] & gt_mask(i, w);
                         c += __popc(x);
