@@ -25,6 +25,7 @@ import oracle as O  # noqa: E402
 from synth import graphs as G  # noqa: E402
 
 PATH = os.path.join(ROOT, "tests", "golden", "configs.json")
+VSET_CAP = 100
 
 
 def _load():
@@ -79,16 +80,20 @@ def main(argv):
             _count_entry("c2", cg, k, threads)
     elif what == "c2edges":
         # per-edge sub-branch counts (Eq. 2) for a deterministic sample of edges: the 8
-        # largest VSets (ties by edge id) and 40 random edges with |VSet| >= k-2
+        # largest VSets of at most VSET_CAP vertices (ties by edge id) and 40 random edges
+        # with k-2 <= |VSet| <= VSET_CAP.  The cap keeps the oracle to minutes: at k = 9 one
+        # sub-branch of 100 vertices in this graph's core already takes ~20 s on one core
+        # and the work grows steeply with |VSet| (the largest is 246)
         g = G.chung_lu()
         cg = O.CleanGraph.of(g)
         lvl, rnd, _ = O.truss_peel(cg)
         vs = O.vset_sizes(cg, rnd).astype(np.int64)
         for k in ks or [9]:
-            order = np.lexsort((np.arange(vs.size), -vs))
+            capped = np.where(vs <= VSET_CAP, vs, -1)
+            order = np.lexsort((np.arange(vs.size), -capped))
             heavy = order[:8]
             rng = np.random.default_rng(k)
-            cand = np.nonzero(vs >= k - 2)[0]
+            cand = np.nonzero((vs >= k - 2) & (vs <= VSET_CAP))[0]
             rand = np.sort(rng.choice(cand, size=min(40, cand.size), replace=False))
             edges = np.unique(np.concatenate([heavy, rand]))
             t = time.time()

@@ -4,7 +4,8 @@ exist, scaled otherwise), through the C ABI, exact integer equality.
 * G(2000, 0.01): counts and listing against the oracle at run time.
 * Chung-Lu power law, n = 1e6 (the bench workload, launched as bench.py launches
   it): graph fingerprint, tau, peel rounds, triangles, and the k = 5 and 7 counts and
-  checksums against tests/golden/configs.json (written by oracle/make_golden.py).
+  checksums against tests/golden/configs.json (written by oracle/make_golden.py); k = 9
+  per edge on sampled edges of up to 100 common neighbours.
 * SBM with exact 2-plex blocks (dense-core stress), scaled to 80-vertex blocks so the
   oracle finishes: whole-graph counts; every 2-plex block against its closed form.
 * A batch of uneven small graphs with their own k: kclique_count_batch against the
@@ -76,6 +77,32 @@ def test_config2_power_law_counts(power_law, k):
     assert str(got["count"]) == GOLD[key]["count"]
     assert str(got["checksum"]) == GOLD[key]["checksum"]
     assert str(K().kclique_count(h, k)["count"]) == GOLD[key]["count"]
+
+
+def test_config2_power_law_k9_per_edge(power_law):
+    """k = 9 on the full power-law graph, per edge: the sub-branch counts and checksums of
+    sampled edges against the oracle's (oracle/make_golden.py c2edges 9).  The run is the
+    ticket shard of all edges with |VSet| <= 100 (tickets are ordered by |VSet| descending),
+    which holds every sampled edge; the heavier sub-branches are left to the bench."""
+    g, h = power_law
+    ref = GOLD.get("c2/edges_k9")
+    if ref is None:
+        pytest.skip("c2/edges_k9 not computed by oracle/make_golden.py")
+    cap = 100
+    vs = K().kclique_edge_data(h)["vset_size"]
+    edges = np.asarray(ref["edges"], dtype=np.int64)
+    assert [int(x) for x in vs[edges]] == ref["vset"] and max(ref["vset"]) <= cap
+    begin, m = int((vs > cap).sum()), g.m
+    ec = torch.zeros(m, dtype=torch.int64, device="cuda")
+    es = torch.zeros(m, dtype=torch.int64, device="cuda")
+    r = K().kclique_count(h, 9, ticket_begin=begin, ticket_end=m, edge_count=ec, edge_checksum=es,
+                          flags=K().KC_CHECKSUM)
+    gc = ec.cpu().numpy().view(np.uint64)
+    gs = es.cpu().numpy().view(np.uint64)
+    assert [str(int(x)) for x in gc[edges]] == ref["count"]
+    assert [str(int(x)) for x in gs[edges]] == ref["checksum"]
+    assert int(gc.astype(object).sum()) == r["count"]
+    assert not gc[vs > cap].any()  # edges outside the shard were not touched
 
 
 def test_config3_sbm_2plex_scaled():
