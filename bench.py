@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 # small frames and one pass takes tens of minutes, so the default step runs k = 5 and 7
 # (see the design doc for the k = 9 shard measurements); --ks 5,7,9 runs all three.
 KS = (5, 7)
+WORKLOAD = "chung_lu n=1e6 m=1.0e7 exp=2.1 wmax=1e4 +200 cliques(30-60)"
 LIST_K = 5
 LIST_CAP = 1 << 24
 METRIC = "k-cliques/s (exact)"
@@ -50,10 +51,16 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", choices=["power_law", "batch", "serve"], default="power_law",
+    ap.add_argument("--workload", choices=["power_law", "batch", "serve", "probe"], default="power_law",
                     help="power_law: the default bench line; batch / serve: the batching and serving "
-                         "measurements (separate JSON lines)")
+                         "measurements (separate JSON lines); probe: one count on a Chung-Lu graph sized "
+                         "by the --probe-* flags, the small case for profiler captures (not a bench value)")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--probe-n", type=int, default=1_000_000)
+    ap.add_argument("--probe-wmax", type=float, default=3000.0)
+    ap.add_argument("--probe-k", type=int, default=7)
+    ap.add_argument("--probe-checksum", action="store_true")
+    ap.add_argument("--probe-tickets", default="", help="b:e -- count only tickets [b, e) (a shard)")
     return ap.parse_args(argv)
 
 
@@ -182,8 +189,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "k-cliques/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "chung_lu n=1e6 m=1.0e7 exp=2.1 wmax=1e4 +200 cliques(30-60), k=5,7,9",
-                       "l2": "n/a (CPU)"},
+            "config": {"workload": WORKLOAD + f", k={','.join(map(str, ks))}", "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": val, "unit": "k-cliques/s", "cores": thr, "kind": "oracle",
                              "sample": f"{tops} random top vertices of the degeneracy-ordered vertex branching, "
                                        f"k in {ks}, {tot_s:.1f} s"},
@@ -298,14 +304,15 @@ def run_serve(args):
         hs = []
         for g in base:
             hs.append(K.kclique_prepare(g.row_ptr, g.col, g.n))
-        out = torch.empty((cap, 10), dtype=torch.int32, device="cuda")
         lat, res = [], []
+        busy = {"count": 0.0, "list": 0.0, "upload": 0.0}
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for (t, kind, gid, k, i) in trace:
             now = time.perf_counter() - t0
             if t > now:
                 time.sleep(t - now)
+            tb = time.perf_counter()
             if kind == "upload":
                 g = uploads[i]
                 K.kclique_prepare(g.row_ptr, g.col, g.n).release()
@@ -319,25 +326,52 @@ def run_serve(args):
                 r = K.kclique_list(hs[gid], k, o)
                 res.append((r["count"], r["checksum"]))
                 lat.append(time.perf_counter() - t0 - t)
+            busy[kind] += time.perf_counter() - tb
         span = time.perf_counter() - t0
         lat.sort()
         nq = len(lat)
         return {"p50_s": lat[nq // 2], "p99_s": lat[min(nq - 1, int(0.99 * (nq - 1)))], "throughput_qps": nq / span,
-                "queries": nq}, res
+                "queries": nq, "busy_s": busy}, res
 
     st_srv, res_srv = replay_server()
     st_fifo, res_fifo = replay_fifo()
     same = all(a is None or r.kind == "upload" or (r.count, r.checksum) == a
                for r, a in zip(res_srv, res_fifo))
+    errors = sorted({r.status for r in res_srv if r.status != "ok" and not r.status.startswith("rejected")})
     line = {"metric": "served k-clique queries/s (continuous batching)", "workload": "serve",
             "value": st_srv["throughput_qps"], "unit": "queries/s", "p50_s": st_srv["p50_s"],
             "p99_s": st_srv["p99_s"], "batches": st_srv["batches"], "mean_batch": st_srv["mean_batch"],
             "rejected": st_srv["rejected"], "one_query_per_launch": st_fifo,
             "speedup": st_srv["throughput_qps"] / st_fifo["throughput_qps"], "results_identical": same,
+            "errors": errors[:5],
             "config": {"arrivals": n_arr, "rate_qps": 2000, "resident": "4 x G(2000,0.01) seeds 0-3 + "
                        "4 x Chung-Lu n=1e5 wmax=2000 seeds 0-3", "k": "U{4..10}", "mix": "35% count, 35% list "
                        "(cap 1024 rows), 30% upload of 4x250 SBM with one 2-plex block", "hbm_budget_GB": 120}}
     print(json.dumps(line), flush=True)
+
+
+def run_probe(args):
+    """Prepare a Chung-Lu graph (n = --probe-n, max expected degree --probe-wmax, seed 0) and
+    run one count at k = --probe-k; prints the count, the branch time and the work counters."""
+    import numpy as np
+    import torch
+
+    from paper_2311_13798_gb300 import kclique as K
+    from synth import graphs as G
+    torch.cuda.set_device(0)
+    g = G.chung_lu(n=args.probe_n, w_max=args.probe_wmax)
+    rp = torch.from_numpy(g.row_ptr.astype(np.int32)).cuda()
+    col = torch.from_numpy(g.col.astype(np.int32)).cuda()
+    h = K.kclique_prepare(rp, col, g.n)
+    flags = K.KC_CHECKSUM if args.probe_checksum else 0
+    tb, te = (int(x) for x in args.probe_tickets.split(":")) if args.probe_tickets else (0, 0)
+    r = K.kclique_count(h, args.probe_k, flags=flags, ticket_begin=tb, ticket_end=te)
+    info = K.kclique_info(h)
+    print(json.dumps({"workload": "probe", "n": g.n, "m": g.m, "w_max": args.probe_wmax, "tau": info["tau"],
+                      "k": args.probe_k, "tickets": [tb, te], "count": str(r["count"]),
+                      "checksum": str(r["checksum"]),
+                      "ms_branch": r["ms_branch"], "word_ops": r["word_ops"], "nodes": r["nodes"],
+                      "et_hits": r["et_hits"], "kernel_rev": K.kclique_kernel_rev()}), flush=True)
 
 
 def main(argv=None):
@@ -350,6 +384,9 @@ def main(argv=None):
         return
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "probe":
+        run_probe(args)
         return
     import numpy as np
     import torch
@@ -468,8 +505,8 @@ def main(argv=None):
         line = {"metric": METRIC, "value": value, "unit": "k-cliques/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-                "config": {"workload": "chung_lu n=1e6 m=1.0e7 exp=2.1 wmax=1e4 +200 cliques(30-60), k=5,7,9 "
-                                       "+ list k=5 cap 2^24", "graph": g.fingerprint(), "m": g.m,
+                "config": {"workload": WORKLOAD + f", k={','.join(map(str, ks))} + list k={LIST_K} cap 2^24",
+                           "graph": g.fingerprint(), "m": g.m,
                            "l2": "flushed (256 MB write) before every step",
                            "ms_prepare": phase["prepare"] / args.steps,
                            "ms_count": {k: v / args.steps for k, v in branch_ms.items()},

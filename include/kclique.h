@@ -73,6 +73,7 @@ typedef enum {
 #define KC_NO_RULE2 0x2u     /* disable pruning Rule (2) (Sec. 4.3) */
 #define KC_CHECKSUM 0x4u     /* also compute the checksum in kclique_count */
 #define KC_NO_RULE1 0x8u     /* disable pruning Rule (1) (Sec. 4.3) */
+#define KC_ROWS_ONLY 0x10u   /* kclique_list: rows only; see kclique_list for the totals */
 
 typedef struct kc_graph kc_graph; /* opaque, device resident, immutable after prepare */
 
@@ -145,6 +146,12 @@ KC_API kc_status kclique_count(const kc_graph *g, uint32_t k, const kc_params *p
  * order unspecified.  If more than cap cliques exist, the first cap found are
  * written, KC_TRUNCATED is returned, r->written = cap, and r->count /
  * r->checksum still cover all cliques.  The checksum is always computed.
+ * The listing pass stops once the buffer is full; the totals then come from a
+ * second pass, a count with checksum (r->ms_* and the work counters cover both).
+ * With KC_ROWS_ONLY in p->flags that second pass is skipped: once the buffer is
+ * full (r->written == cap) the call returns KC_TRUNCATED with r->count and
+ * r->checksum 0 (the caller counts separately); otherwise they are the exact
+ * totals as always.
  */
 KC_API kc_status kclique_list(const kc_graph *g, uint32_t k, uint32_t *d_out, uint64_t cap,
                        const kc_params *p, kc_stream s, kc_result *r);

@@ -110,22 +110,50 @@ kc_status run_one(const kc_graph *g, u32 k, const kc_params *p, cudaStream_t s, 
     kc_dev_acc acc;
     memset(&acc, 0, sizeof(acc));
     float ms = 0.f, msb = 0.f;
+    // listing: one pass writes rows and, when every clique fits, also yields the exact
+    // totals; once the buffer is full it stops, and the totals come from a count with
+    // checksum instead (which may split heavy sub-branches; a listing pass cannot)
+    cfg.stop_full = list;
     st = kc_run_queries(&q, 1, &cfg, s, &acc, &ms, &msb);
     if (st != KC_OK) return st;
     st = map_device_status(acc.status);
     if (st != KC_OK) return st;
-    r->count_lo = acc.count_lo;
-    r->count_hi = acc.count_hi;
-    r->checksum = (list || (cfg.flags & KC_CHECKSUM)) ? acc.checksum : 0ull;
-    r->written = list ? std::min<u64>(acc.written, cap) : 0ull;
+    const u64 written = acc.written;
+    u64 extra_ops = 0, extra_nodes = 0, extra_pairs = 0;
+    const bool rows_only = p && (p->flags & KC_ROWS_ONLY);
+    if (list && written >= cap && !rows_only) {
+        extra_ops = acc.word_ops;
+        extra_nodes = acc.nodes;
+        extra_pairs = acc.pair_tests;
+        kc_run_cfg cc = cfg;
+        cc.list = 0;
+        cc.stop_full = 0;
+        cc.d_out = nullptr;
+        cc.cap = 0;
+        cc.flags |= KC_CHECKSUM;
+        float ms2 = 0.f, msb2 = 0.f;
+        memset(&acc, 0, sizeof(acc));
+        st = kc_run_queries(&q, 1, &cc, s, &acc, &ms2, &msb2);
+        if (st != KC_OK) return st;
+        st = map_device_status(acc.status);
+        if (st != KC_OK) return st;
+        ms += ms2;
+        msb += msb2;
+    }
+    const bool no_totals = list && written >= cap && rows_only;
+    r->count_lo = no_totals ? 0ull : acc.count_lo;
+    r->count_hi = no_totals ? 0ull : acc.count_hi;
+    r->checksum = (list || (cfg.flags & KC_CHECKSUM)) && !no_totals ? acc.checksum : 0ull;
+    r->written = list ? std::min<u64>(written, cap) : 0ull;
     r->edge_branches = acc.branches;
-    r->nodes = acc.nodes;
+    r->nodes = acc.nodes + extra_nodes;
     r->et_hits = acc.et_hits;
-    r->word_ops = acc.word_ops;
-    r->pair_tests = acc.pair_tests;
+    r->word_ops = acc.word_ops + extra_ops;
+    r->pair_tests = acc.pair_tests + extra_pairs;
     r->ms_count = ms;
     r->ms_branch = msb;
-    if (list && acc.written > cap) return KC_TRUNCATED;
+    if (no_totals) return KC_TRUNCATED;  // the buffer filled: totals unknown
+    if (list && (acc.count_hi != 0 || acc.count_lo > cap)) return KC_TRUNCATED;
     return KC_OK;
 }
 

@@ -28,9 +28,37 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "kc_internal.cuh"
+
+// build-time tuning knobs (same results for every value)
+#ifndef KC_SCAN_RATIO  // extraction scans a row when its length <= ratio x candidates left
+#define KC_SCAN_RATIO 4
+#endif
+#ifndef KC_ITEM_MINB8  // resident blocks per SM asked of the compiler, item kernel, W = 8
+#define KC_ITEM_MINB8 5   // (5: 96 registers; 4.5 % faster than 4 on the power-law k = 7 run)
+#endif
+#ifndef KC_LANE_ET_MAX  // l = 3 children up to this size get the in-lane plex test; larger ones
+#define KC_LANE_ET_MAX 1024  // go to the warp routine, which tests them too
+#endif
+#ifndef KC_SECTION_PROFILE  // 1: per-section cycle counters (KC_PROFILE=1 at run time)
+#define KC_SECTION_PROFILE 0
+#endif
+#ifndef KC_DEBUG_BOUNDS  // 1: self-checking build (bounds of computed shared-memory indices)
+#define KC_DEBUG_BOUNDS 0
+#endif
+#ifndef KC_ROW_PAD     // words of padding after each adjacency row (odd stride: no bank conflicts)
+#define KC_ROW_PAD 1
+#endif
+#ifndef KC_PRECHECK    // per-u plex pre-check masks for l = 3 children (count mode); off:
+#define KC_PRECHECK 0  // on the power-law workload the masks cost more than they saved
+#endif
+
+#ifndef KC_DYN_SMEM  // dynamic shared memory of a kernel (a host emulation of the kernels redefines it)
+#define KC_DYN_SMEM(name) extern __shared__ __align__(16) unsigned char name[]
+#endif
 
 namespace {
 
@@ -70,16 +98,29 @@ struct Args {
     unsigned char *slots;           // [slot_cap] published sub-branches (nullptr: no splitting)
     unsigned long long *slot_ctr;
     u64 slot_cap;
-    u64 *items;                     // [item_cap] (slot << 32) | u
-    unsigned long long *item_ctr;   // items written
-    unsigned long long *item_next;  // items taken
-    u64 item_cap;
+    unsigned long long *slot_next;  // slots taken by branch_items_kernel blocks
     u32 *d_out;
     u64 cap;
+    u32 stop_full;      // list: leave once the buffer is full
+    u32 pad_;
     const u128 *binom;
+    unsigned long long *l3hist;  // profiling only: [2][8] l = 3 frames and their cycles by size
 };
 
 // ---------------------------------------------------------------- helpers
+#if KC_DEBUG_BOUNDS
+// first violation: (source line << 40) | (index & 0xFFFFF) << 20 | (bound & 0xFFFFF)
+__device__ unsigned long long g_kc_dbg;
+__device__ __noinline__ bool kc_dbg_ok(long long i, long long n, int line) {
+    if (i >= 0 && i < n) return true;
+    atomicCAS(&g_kc_dbg, 0ull, ((unsigned long long)line << 40) | ((unsigned long long)(i & 0xFFFFF) << 20) |
+                                   (unsigned long long)(n & 0xFFFFF));
+    return false;
+}
+#define KC_OK(i, n) kc_dbg_ok((long long)(i), (long long)(n), __LINE__)
+#else
+#define KC_OK(i, n) true
+#endif
 __device__ __forceinline__ u64 zkey(u64 v) {
     u64 x = v + 0x9E3779B97F4A7C15ull;
     x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -145,7 +186,8 @@ __device__ __forceinline__ u128 warp_sum_u128(u64 x) {
 
 // ---------------------------------------------------------------- smem layout
 struct Lay {
-    u32 *A;          // [S][W] adjacency rows (undirected, positions)
+    u32 *A;          // [S][W + KC_ROW_PAD] adjacency rows (undirected, positions); an odd
+                     // row stride puts word w of 32 different rows in 32 different banks
     u32 *C0;         // [W] top frame
     u32 *vid;        // [S] vertex id per position
     u64 *z;          // [S] key per position
@@ -165,7 +207,8 @@ struct Lay {
     u32 *path;       // [2D+4]
     uint16_t *bu, *bv;  // [32]
     uint8_t *bs;        // [32] ring slot of each batch entry's u (plex pre-check)
-    u32 *Bm, *M1;       // [D][4][W] per-u masks of the last 4 u's at each depth (plex pre-check)
+    u32 *Bm, *M1;       // [4][W] per-u masks of the last 4 u's (plex pre-check; only the one
+                        // depth whose frames have l = 5 uses them)
     int *rn;            // [D] u's entered into the ring so far
     u32 *tmpW;       // [W]
     u32 *tmpW2;      // [W]
@@ -174,57 +217,71 @@ struct Lay {
 template <int W>
 __host__ __device__ constexpr u32 align16(u32 x) { return (x + 15u) & ~15u; }
 
+// The frame of a sub-branch (adjacency, ids, keys, colours, Rule 1/2 tables) is read-only
+// once extracted and coloured; the item kernel keeps one copy per block, shared by its
+// warps.  Everything else is per-warp DFS state.
 template <int W>
-__host__ __device__ u32 lay_bytes(u32 D, bool sum) {
+__host__ __device__ u32 frame_bytes(bool sum) {
     const u32 S = 32u * W;
     u32 b = 0;
-    b += align16<W>(4u * S * W);       // A
-    b += align16<W>(4u * W);           // C0
+    b += align16<W>(4u * S * (W + KC_ROW_PAD)); // A
     b += align16<W>(4u * S);           // vid
     b += sum ? align16<W>(8u * S) : 0u;  // z (checksum / listing only)
     b += align16<W>(2u * S);           // col
-    b += align16<W>(2u * S);           // aux
-    b += align16<W>(2u * S);           // aux2
     b += align16<W>(2u * (S + 2));     // lim
     b += align16<W>(8u * W);           // J, E
+    return b;
+}
+
+// per-warp bytes; shared_frame: the frame lives elsewhere (one per block)
+template <int W>
+__host__ __device__ u32 lay_bytes(u32 D, bool sum, bool shared_frame = false) {
+    const u32 S = 32u * W;
+    u32 b = shared_frame ? 0u : frame_bytes<W>(sum);
+    b += align16<W>(4u * W);           // C0
+    b += align16<W>(2u * S);           // aux
+    b += align16<W>(2u * S);           // aux2
     b += align16<W>(4u * D * W);       // V
     b += align16<W>(16u * D);          // cur, nchild, nextc, slot
     b += align16<W>(4u * D * 32 * W);  // childC
-    b += align16<W>(8u * D * 32);      // childP
+    b += sum ? align16<W>(8u * D * 32) : 0u;  // childP (checksum / listing only)
     b += align16<W>(4u * D * 32);      // childUV
     b += align16<W>(4u * (2 * D + 4)); // path
     b += align16<W>(2u * 64);          // bu, bv
     b += align16<W>(32u);              // bs
-    b += align16<W>(2u * 4u * D * 4 * W);  // Bm, M1
+    b += KC_PRECHECK ? align16<W>(2u * 4u * 4 * W) : 0u;  // Bm, M1
     b += align16<W>(4u * D);           // rn
     b += align16<W>(8u * W);           // tmpW, tmpW2
     return b;
 }
 
+// p: this warp's bytes; frame: the shared frame (nullptr: the frame is at the start of p)
 template <int W>
-__device__ Lay make_lay(unsigned char *p, u32 D, bool sum) {
+__host__ __device__ Lay make_lay(unsigned char *p, u32 D, bool sum, unsigned char *frame = nullptr) {
     const u32 S = 32u * W;
     Lay L;
+    unsigned char *f = frame ? frame : p;
     u32 o = 0;
-    L.A = (u32 *)(p + o); o += align16<W>(4u * S * W);
+    L.A = (u32 *)(f + o); o += align16<W>(4u * S * (W + KC_ROW_PAD));
+    L.vid = (u32 *)(f + o); o += align16<W>(4u * S);
+    L.z = (u64 *)(f + o); o += sum ? align16<W>(8u * S) : 0u;
+    L.col = (uint16_t *)(f + o); o += align16<W>(2u * S);
+    L.lim = (uint16_t *)(f + o); o += align16<W>(2u * (S + 2));
+    L.J = (u32 *)(f + o); L.E = L.J + W; o += align16<W>(8u * W);
+    if (frame) o = 0;
     L.C0 = (u32 *)(p + o); o += align16<W>(4u * W);
-    L.vid = (u32 *)(p + o); o += align16<W>(4u * S);
-    L.z = (u64 *)(p + o); o += sum ? align16<W>(8u * S) : 0u;
-    L.col = (uint16_t *)(p + o); o += align16<W>(2u * S);
     L.aux = (uint16_t *)(p + o); o += align16<W>(2u * S);
     L.aux2 = (uint16_t *)(p + o); o += align16<W>(2u * S);
-    L.lim = (uint16_t *)(p + o); o += align16<W>(2u * (S + 2));
-    L.J = (u32 *)(p + o); L.E = L.J + W; o += align16<W>(8u * W);
     L.V = (u32 *)(p + o); o += align16<W>(4u * D * W);
     L.cur = (int *)(p + o); L.nchild = L.cur + D; L.nextc = L.nchild + D; L.slot = L.nextc + D;
     o += align16<W>(16u * D);
     L.childC = (u32 *)(p + o); o += align16<W>(4u * D * 32 * W);
-    L.childP = (u64 *)(p + o); o += align16<W>(8u * D * 32);
+    L.childP = (u64 *)(p + o); o += sum ? align16<W>(8u * D * 32) : 0u;
     L.childUV = (u32 *)(p + o); o += align16<W>(4u * D * 32);
     L.path = (u32 *)(p + o); o += align16<W>(4u * (2 * D + 4));
     L.bu = (uint16_t *)(p + o); L.bv = L.bu + 32; o += align16<W>(2u * 64);
     L.bs = (uint8_t *)(p + o); o += align16<W>(32u);
-    L.Bm = (u32 *)(p + o); L.M1 = L.Bm + D * 4 * W; o += align16<W>(2u * 4u * D * 4 * W);
+    L.Bm = (u32 *)(p + o); L.M1 = L.Bm + 4 * W; o += KC_PRECHECK ? align16<W>(2u * 4u * 4 * W) : 0u;
     L.rn = (int *)(p + o); o += align16<W>(4u * D);
     L.tmpW = (u32 *)(p + o); L.tmpW2 = L.tmpW + W; o += align16<W>(8u * W);
     return L;
@@ -276,12 +333,12 @@ __device__ bool permute(const Lay &L, int s, int lane, uint16_t *extra16) {
         src[w] = r < s ? ord[r] : -1;
     }
     for (int r = 0; r < s; r++) {
-        u32 *row = L.A + r * W;
+        u32 *row = L.A + r * (W + KC_ROW_PAD);
         u32 mine = 0;
 #pragma unroll
         for (int w = 0; w < W; w++) {
             int sp = src[w];
-            bool bit = sp >= 0 && ((row[sp >> 5] >> (sp & 31)) & 1u);
+            bool bit = sp >= 0 && KC_OK(sp, s) && ((row[sp >> 5] >> (sp & 31)) & 1u);
             u32 bal = __ballot_sync(0xffffffffu, bit);
             if (lane == w) mine = bal;
         }
@@ -294,23 +351,26 @@ __device__ bool permute(const Lay &L, int s, int lane, uint16_t *extra16) {
     __syncwarp();
     int steps = 0;
     for (int st = 0; st < s; st++) {
-        bool vis = (L.tmpW2[st >> 5] >> (st & 31)) & 1u;
+        // lane 0 sets visited bits below; every lane takes lane 0's reading (the shuffle
+        // also orders all lanes' reads before lane 0's next write)
+        const int vis = __shfl_sync(0xffffffffu, (int)((L.tmpW2[st >> 5] >> (st & 31)) & 1u), 0);
         if (vis) continue;
-        u32 keep = lane < W ? L.A[st * W + lane] : 0;
+        u32 keep = lane < W ? L.A[st * (W + KC_ROW_PAD) + lane] : 0;
         int j = st;
         while (true) {
             if (++steps > s) return false;  // not a permutation: bounded, reported by the caller
             int sp = ord[j];
+            if (!KC_OK(sp, s) || !KC_OK(j, s)) return false;
             if (lane == 0) L.tmpW2[j >> 5] |= 1u << (j & 31);
             if (sp == st) {
                 __syncwarp();
-                if (lane < W) L.A[j * W + lane] = keep;
+                if (lane < W) L.A[j * (W + KC_ROW_PAD) + lane] = keep;
                 __syncwarp();
                 break;
             }
-            u32 t = lane < W ? L.A[sp * W + lane] : 0;
+            u32 t = lane < W ? L.A[sp * (W + KC_ROW_PAD) + lane] : 0;
             __syncwarp();
-            if (lane < W) L.A[j * W + lane] = t;
+            if (lane < W) L.A[j * (W + KC_ROW_PAD) + lane] = t;
             __syncwarp();
             j = sp;
         }
@@ -318,7 +378,7 @@ __device__ bool permute(const Lay &L, int s, int lane, uint16_t *extra16) {
     // per-position arrays, gathered through shared scratch (the child-frame buffers,
     // unused while a sub-branch is being renumbered); keys are recomputed from ids
     u32 *tmp = L.childC;
-    for (int r = lane; r < s; r += 32) tmp[r] = L.vid[ord[r]];
+    for (int r = lane; r < s; r += 32) tmp[r] = KC_OK(ord[r], s) ? L.vid[ord[r]] : 0u;
     __syncwarp();
     for (int r = lane; r < s; r += 32) L.vid[r] = tmp[r];
     __syncwarp();
@@ -340,59 +400,84 @@ struct Acc {
     u64 nodes, et;  // per lane (lane 0 counts)
     u64 ops;        // per lane: algorithmic word-ops (3 per word of an intersection, 2 per degree word)
     u64 pairs;      // per lane: adjacency tests during extraction
+#if KC_SECTION_PROFILE
     u64 sec[6];     // lane 0, profiling: extract, colour, ET (l >= 4), l=3 frames, generate, evaluate
+#endif
     u32 status;
 };
 
 // ---------------------------------------------------------------- A5 extraction
 template <int W>
 __device__ void extract(const Lay &L, const QDesc &q, int s, u32 e, u32 re, int lane, Acc &acc) {
-    for (int i = lane; i < s * W; i += 32) L.A[i] = 0;
+    constexpr int RS = W + KC_ROW_PAD;
+    for (int i = lane; i < s * RS; i += 32) L.A[i] = 0;
     __syncwarp();
     const u32 vmax = L.vid[s - 1];
-    for (int i = 0; i + 1 < s; i++) {
-        const u32 x = L.vid[i];
-        u32 xb = q.row_ptr[x], xe = q.row_ptr[x + 1];
-        // restrict the row to (x, vmax]
-        {
-            u32 lo = xb, hi = xe;
+    // rows in batches of 32: lane r restricts row ib + r to its columns in (x, vmax] (two
+    // binary searches, 32 rows in flight at once), then the warp runs over the batch's
+    // (row, item) pairs as one flat list, so short and long rows share the lanes evenly
+    for (int ib = 0; ib + 1 < s; ib += 32) {
+        const int i = ib + lane;
+        u32 xb = 0, xe = 0;
+        int work = 0, scan = 1;
+        if (i + 1 < s) {
+            const u32 x = L.vid[i];
+            const u32 rb = q.row_ptr[x], re_ = q.row_ptr[x + 1];
+            u32 lo = rb, hi = re_;
             while (lo < hi) { u32 mid = (lo + hi) >> 1; if (q.col[mid] <= x) lo = mid + 1; else hi = mid; }
             xb = lo;
-            lo = xb; hi = xe;
+            hi = re_;
             while (lo < hi) { u32 mid = (lo + hi) >> 1; if (q.col[mid] <= vmax) lo = mid + 1; else hi = mid; }
             xe = lo;
+            const int rem = s - 1 - i;
+            // scan the row (coalesced loads, binary search in shared vid) unless it is much
+            // longer than the candidates; then search each candidate in the row instead
+            scan = (xe - xb) <= (u32)KC_SCAN_RATIO * (u32)rem;
+            work = scan ? (int)(xe - xb) : rem;
         }
-        const u32 dx = xe - xb;
-        const int rem = s - 1 - i;
-        // scan the row (coalesced global loads, binary search in shared vid) unless it is
-        // much longer than the candidates; dependent global binary searches are latency bound
-        if (dx <= 32u * (u32)rem) {
-            for (u32 p = xb + lane; p < xe; p += 32) {
-                acc.pairs++;
-                u32 y = q.col[p];
-                int lo = i + 1, hi = s;
-                while (lo < hi) { int mid = (lo + hi) >> 1; if (L.vid[mid] < y) lo = mid + 1; else hi = mid; }
-                if (lo < s && L.vid[lo] == y) {
-                    u32 rr = q.pos_round[p], ee = q.pos_eid[p];
-                    if (rr > re || (rr == re && ee > e)) {
-                        int j = lo;
-                        atomicOr(&L.A[i * W + (j >> 5)], 1u << (j & 31));
-                        atomicOr(&L.A[j * W + (i >> 5)], 1u << (i & 31));
-                    }
-                }
+        int off = work;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, off, o);
+            if (lane >= o) off += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, off, 31);
+        off -= work;  // exclusive prefix
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            // the row of item t: the last lane r with off_r <= t (it has work_r > t - off_r)
+            int r = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int o2 = __shfl_sync(0xffffffffu, off, r + step);
+                if (o2 <= t) r += step;
             }
-        } else {
-            for (int j = i + 1 + lane; j < s; j += 32) {
-                acc.pairs++;
-                u32 y = L.vid[j];
-                u32 lo = xb, hi = xe;
+            const u32 xb_r = __shfl_sync(0xffffffffu, xb, r);
+            const u32 xe_r = __shfl_sync(0xffffffffu, xe, r);
+            const int scan_r = __shfl_sync(0xffffffffu, scan, r);
+            const int k = t - __shfl_sync(0xffffffffu, off, r);
+            if (t >= total) continue;
+            const int ir = ib + r;
+            acc.pairs++;
+            int j = -1;
+            u32 p = 0;
+            if (scan_r) {
+                p = xb_r + (u32)k;
+                const u32 y = q.col[p];
+                int lo = ir + 1, hi = s;
+                while (lo < hi) { int mid = (lo + hi) >> 1; if (L.vid[mid] < y) lo = mid + 1; else hi = mid; }
+                if (lo < s && L.vid[lo] == y) j = lo;
+            } else {
+                const int jj = ir + 1 + k;
+                const u32 y = L.vid[jj];
+                u32 lo = xb_r, hi = xe_r;
                 while (lo < hi) { u32 mid = (lo + hi) >> 1; if (q.col[mid] < y) lo = mid + 1; else hi = mid; }
-                if (lo < xe && q.col[lo] == y) {
-                    u32 rr = q.pos_round[lo], ee = q.pos_eid[lo];
-                    if (rr > re || (rr == re && ee > e)) {
-                        atomicOr(&L.A[i * W + (j >> 5)], 1u << (j & 31));
-                        atomicOr(&L.A[j * W + (i >> 5)], 1u << (i & 31));
-                    }
+                if (lo < xe_r && q.col[lo] == y) { j = jj; p = lo; }
+            }
+            if (j >= 0) {
+                const u32 rr = q.pos_round[p], ee = q.pos_eid[p];
+                if ((rr > re || (rr == re && ee > e)) && KC_OK(ir, s) && KC_OK(j, s)) {
+                    atomicOr(&L.A[ir * RS + (j >> 5)], 1u << (j & 31));
+                    atomicOr(&L.A[j * RS + (ir >> 5)], 1u << (ir & 31));
                 }
             }
         }
@@ -410,7 +495,7 @@ __device__ int colour_and_order(const Lay &L, int s, int lane) {  // -1: interna
     for (int i = lane; i < s; i += 32) {
         int d = 0;
 #pragma unroll
-        for (int w = 0; w < W; w++) d += __popc(L.A[i * W + w]);
+        for (int w = 0; w < W; w++) d += __popc(L.A[i * (W + KC_ROW_PAD) + w]);
         L.aux[i] = (uint16_t)d;
     }
     __syncwarp();
@@ -421,7 +506,7 @@ __device__ int colour_and_order(const Lay &L, int s, int lane) {  // -1: interna
             int dj = L.aux[j];
             r += (dj > di) || (dj == di && j < i);
         }
-        L.aux2[r] = (uint16_t)i;
+        if (KC_OK(r, s)) L.aux2[r] = (uint16_t)i;
     }
     __syncwarp();
     if (!permute<W>(L, s, lane, nullptr)) return -1;
@@ -441,12 +526,12 @@ __device__ int colour_and_order(const Lay &L, int s, int lane) {  // -1: interna
             int fl = __ffs(bal) - 1;
             u32 wv = __shfl_sync(0xffffffffu, S, fl);
             int x = fl * 32 + __ffs(wv) - 1;
-            if (lane == 0) { L.col[x] = (uint16_t)c; L.aux[x] = (uint16_t)k; }
+            if (lane == 0 && KC_OK(x, s)) { L.col[x] = (uint16_t)c; L.aux[x] = (uint16_t)k; }
             k++;
             if (lane == fl) { R &= ~(1u << (x & 31)); S &= ~(1u << (x & 31)); }
-            if (lane < W) S &= ~L.A[x * W + lane];
+            if (lane < W) S &= ~L.A[x * (W + KC_ROW_PAD) + lane];
         }
-        if (lane == 0) L.lim[c] = (uint16_t)k;  // class size for now
+        if (lane == 0 && KC_OK(c, 32 * W + 2)) L.lim[c] = (uint16_t)k;  // class size for now
     }
     const int ncol = c;
     __syncwarp();
@@ -462,7 +547,7 @@ __device__ int colour_and_order(const Lay &L, int s, int lane) {  // -1: interna
     for (int x = lane; x < s; x += 32) {
         int cx = L.col[x];
         int np = L.lim[cx + 1] + L.aux[x];
-        L.aux2[np] = (uint16_t)x;
+        if (KC_OK(np, s)) L.aux2[np] = (uint16_t)x;
     }
     __syncwarp();
     if (!permute<W>(L, s, lane, L.col)) return -1;
@@ -506,6 +591,7 @@ __device__ void write_clique(u32 *out, u64 slot, u32 k, const u32 *ids, int nids
         q[j + 1] = x;
     }
     u32 *dst = out + slot * k;
+    if (!KC_OK(nids, (int)k + 1)) return;
     for (int i = 0; i < nids; i++) dst[i] = q[i];
 }
 
@@ -534,7 +620,7 @@ __device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l
             int x = select_bit<W>(cw, i);
             d = 0;
 #pragma unroll
-            for (int w = 0; w < W; w++) d += __popc(L.A[x * W + w] & cw[w]);
+            for (int w = 0; w < W; w++) d += __popc(L.A[x * (W + KC_ROW_PAD) + w] & cw[w]);
             L.aux2[i] = (uint16_t)x;
             L.aux[i] = (uint16_t)d;
             acc.ops += 2u * (u32)ws;
@@ -575,7 +661,7 @@ __device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l
             } else {
                 // partner: the one non-neighbour of x inside C
                 u32 nb = 0;
-                if (lane < W) nb = C[lane] & ~L.A[x * W + lane] & ~((lane == (x >> 5)) ? (1u << (x & 31)) : 0u);
+                if (lane < W) nb = C[lane] & ~L.A[x * (W + KC_ROW_PAD) + lane] & ~((lane == (x >> 5)) ? (1u << (x & 31)) : 0u);
                 unsigned bal = __ballot_sync(0xffffffffu, nb != 0);
                 int fl = __ffs(bal) - 1;
                 u32 wv = __shfl_sync(0xffffffffu, nb, fl);
@@ -645,7 +731,7 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
             const int x = select_bit<W>(cw, i);
             int d = 0;
 #pragma unroll
-            for (int w = 0; w < W; w++) d += __popc(L.A[x * W + w] & cw[w]);
+            for (int w = 0; w < W; w++) d += __popc(L.A[x * (W + KC_ROW_PAD) + w] & cw[w]);
             L.aux2[i] = (uint16_t)x;
             L.aux[i] = (uint16_t)d;
             const int db = cnt - 1 - d;
@@ -692,7 +778,7 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
                         int y = -1;
 #pragma unroll
                         for (int w = 0; w < W; w++) {
-                            const u32 nb = cw[w] & ~L.A[x * W + w] & ~((w == (x >> 5)) ? (1u << (x & 31)) : 0u);
+                            const u32 nb = cw[w] & ~L.A[x * (W + KC_ROW_PAD) + w] & ~((w == (x >> 5)) ? (1u << (x & 31)) : 0u);
                             if (y < 0 && nb) y = w * 32 + __ffs(nb) - 1;
                         }
                         if (y > x) poly3_mul(p1, p2, p3, L.z[x] + L.z[y], 0ull, 0ull);
@@ -714,7 +800,7 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
             u32 row[W];
 #pragma unroll
             for (int w = 0; w < W; w++) {
-                const u32 ax = comp ? ~L.A[x * W + w] : L.A[x * W + w];
+                const u32 ax = comp ? ~L.A[x * (W + KC_ROW_PAD) + w] : L.A[x * (W + KC_ROW_PAD) + w];
                 row[w] = ax & cw[w] & gt_mask(x, w);
             }
             const u64 zx = SUM ? L.z[x] : 0ull;
@@ -723,7 +809,7 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
                 u64 f1 = 0, f2 = 0;
 #pragma unroll (W <= 8 ? W : 1)
                 for (int w = 0; w < W; w++) {
-                    u32 nb = cw[w] & ~L.A[x * W + w] & ~((w == (x >> 5)) ? (1u << (x & 31)) : 0u);
+                    u32 nb = cw[w] & ~L.A[x * (W + KC_ROW_PAD) + w] & ~((w == (x >> 5)) ? (1u << (x & 31)) : 0u);
                     while (nb) {
                         const u64 z = L.z[w * 32 + __ffs(nb) - 1];
                         nb &= nb - 1;
@@ -733,18 +819,20 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
                 }
                 zsum += zx * f2;
             }
+            // y runs over row in increasing order and leaves it as it goes, so row holds
+            // exactly the candidates z > y and no word below y's has any left
 #pragma unroll (W <= 8 ? W : 1)
             for (int w = 0; w < W; w++) {
-                u32 bits = row[w];
-                while (bits) {
-                    const int y = w * 32 + __ffs(bits) - 1;
-                    bits &= bits - 1;
+                while (row[w]) {
+                    const int y = w * 32 + __ffs(row[w]) - 1;
+                    row[w] &= row[w] - 1;
                     int tc = 0;
                     u64 zw = 0;
 #pragma unroll
                     for (int w2 = 0; w2 < W; w2++) {
-                        const u32 ay = comp ? ~L.A[y * W + w2] : L.A[y * W + w2];
-                        u32 tb = row[w2] & ay & gt_mask(y, w2);
+                        if (w2 < w) continue;
+                        const u32 ay = comp ? ~L.A[y * (W + KC_ROW_PAD) + w2] : L.A[y * (W + KC_ROW_PAD) + w2];
+                        u32 tb = row[w2] & ay;
                         tc += __popc(tb);
                         if (SUM) {
                             while (tb) { zw += L.z[w2 * 32 + __ffs(tb) - 1]; tb &= tb - 1; }
@@ -790,7 +878,7 @@ struct MinBlocks {
 // A heavy sub-branch published for splitting (A12): the coloured, renumbered
 // adjacency of g_e plus what a helper warp needs to rebuild its frames.
 struct SlotHdr {
-    u32 e, s, qi, pad;
+    u32 e, s, qi, limu;  // edge, |VSet|, query, top-frame vertices u to branch on (Rule 1)
     u64 P0, pad2;
 };
 
@@ -817,8 +905,10 @@ __device__ void flush_query(const Args &a, Acc &acc, WarpTotals &wt, int lane, b
     if (lane == 0) {
         atomicAdd(&q.acc->word_ops, (unsigned long long)ops);
         atomicAdd(&q.acc->pair_tests, (unsigned long long)pairs);
+#if KC_SECTION_PROFILE
         if (prof)
             for (int i = 0; i < 6; i++) atomicAdd(&q.acc->sec[i], (unsigned long long)acc.sec[i]);
+#endif
         u64 lo = (u64)wt.q_total, hi = (u64)(wt.q_total >> 64);
         if (lo | hi) {
             unsigned long long old = atomicAdd(&q.acc->count_lo, (unsigned long long)lo);
@@ -833,7 +923,9 @@ __device__ void flush_query(const Args &a, Acc &acc, WarpTotals &wt, int lane, b
     }
     wt.q_total = 0; wt.q_csum = 0; wt.branches = 0;
     acc.nodes = 0; acc.et = 0; acc.status = 0; acc.ops = 0; acc.pairs = 0;
+#if KC_SECTION_PROFILE
     for (int i = 0; i < 6; i++) acc.sec[i] = 0;
+#endif
 }
 
 __device__ __forceinline__ void reset_unit(Acc &acc) {
@@ -860,10 +952,16 @@ __device__ void finish_unit(const QDesc &q, u32 e, Acc &acc, WarpTotals &wt, int
     }
 }
 
-#define KC_SEC_BEGIN() \
-    if (prof) tsec = clock64()
-#define KC_SEC_END(i) \
+#if KC_SECTION_PROFILE
+#define KC_SEC_ADD(i) \
     if (prof && lane == 0) acc.sec[i] += (u64)(clock64() - tsec)
+#else
+#define KC_SEC_ADD(i) (void)tsec
+#endif
+#define KC_SEC_BEGIN() \
+    if (KC_SECTION_PROFILE && prof) tsec = clock64()
+#define KC_SEC_END(i) \
+    KC_SEC_ADD(i)
 
 // A7-A9: depth-first search over the frames of one sub-branch whose coloured,
 // renumbered adjacency is in L.  The top frame is C0 = {0..s-1} with l = l0; its
@@ -893,10 +991,21 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
         if (phase == 0) {
             if (lane == 0) acc.nodes++;
             if (LIST) full = *(volatile unsigned long long *)&q.acc->written >= a.cap;
+            // rows only: the totals come from a separate count
+            if (LIST && a.stop_full && __shfl_sync(0xffffffffu, (int)full, 0)) break;
             if (l == 3 && (!LIST || full)) {
+                const long long tf = (KC_SECTION_PROFILE && prof) ? clock64() : 0;
                 KC_SEC_BEGIN();
                 frame_l3_count<W, SUM>(L, C, lane, acc, (int)a.t_max, use_et, Ws, P);
                 KC_SEC_END(3);
+                if (KC_SECTION_PROFILE && prof && a.l3hist) {
+                    const int c = warp_popc<W>(C, lane);
+                    if (lane == 0) {
+                        const int b = c <= 8 ? 0 : c <= 16 ? 1 : c <= 32 ? 2 : c <= 64 ? 3 : c <= 128 ? 4 : c <= 256 ? 5 : 6;
+                        atomicAdd(&a.l3hist[b], 1ull);
+                        atomicAdd(&a.l3hist[8 + b], (unsigned long long)(clock64() - tf));
+                    }
+                }
                 phase = 3;
                 continue;
             }
@@ -920,7 +1029,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
             u32 *V = L.V + d * W;
             int u = L.cur[d];
             // plex pre-check for l = 3 children (count mode): masks of the current u
-            const bool pre = !SUM && l == 5 && use_et;
+            const bool pre = KC_PRECHECK && !SUM && l == 5 && use_et;
             int nuniq = 0;  // distinct u's in this batch (at most 4: the ring)
             if (pre) {
                 u32 vw0 = lane < W ? V[lane] : 0u;
@@ -936,8 +1045,9 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                     int nu = warp_first_from<W>(C, u + 1, lane);
                     if (nu < 0 || nu >= limu) { u = -2; break; }
                     u = nu;
+                    if (!KC_OK(u, s)) { u = -2; break; }
                     u32 nv = 0;
-                    if (lane < W) nv = L.A[u * W + lane] & C[lane] & gt_mask(u, lane) & lt_mask(limv, lane);
+                    if (lane < W) nv = L.A[u * (W + KC_ROW_PAD) + lane] & C[lane] & gt_mask(u, lane) & lt_mask(limv, lane);
                     if (lane < W) V[lane] = nv;
                     if (pre && __any_sync(0xffffffffu, nv != 0)) {
                         // over Cu = C & N(u) & {> u}: B = vertices with >= t_max non-neighbours
@@ -947,10 +1057,10 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                         int ncu = 0;
 #pragma unroll
                         for (int w = 0; w < W; w++) {
-                            cu[w] = C[w] & L.A[u * W + w] & gt_mask(u, w);
+                            cu[w] = C[w] & L.A[u * (W + KC_ROW_PAD) + w] & gt_mask(u, w);
                             ncu += __popc(cu[w]);
                         }
-                        u32 *Bm = L.Bm + (d * 4 + slot) * W, *M1 = L.M1 + (d * 4 + slot) * W;
+                        u32 *Bm = L.Bm + slot * W, *M1 = L.M1 + slot * W;
                         if (lane < W) { Bm[lane] = 0; M1[lane] = 0; }
                         __syncwarp();
                         const int tm = (int)a.t_max;
@@ -960,7 +1070,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                                 const int x = select_bit<W>(cu, i);
                                 int md = -1;  // x itself is not in N(x)
 #pragma unroll
-                                for (int w = 0; w < W; w++) md += __popc(cu[w] & ~L.A[x * W + w]);
+                                for (int w = 0; w < W; w++) md += __popc(cu[w] & ~L.A[x * (W + KC_ROW_PAD) + w]);
                                 if (md >= tm) atomicOr(&Bm[x >> 5], 1u << (x & 31));
                                 if (md >= 1) atomicOr(&M1[x >> 5], 1u << (x & 31));
                                 acc.ops += 2u * (u32)Ws;
@@ -985,6 +1095,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                 for (int i = 0; i < take; i++) {
                     int b = __ffs(vw) - 1;
                     vw &= vw - 1;
+                    if (!KC_OK(nb + off + i, 32) || !KC_OK(lane * 32 + b, s)) continue;
                     L.bu[nb + off + i] = (uint16_t)u;
                     L.bv[nb + off + i] = (uint16_t)(lane * 32 + b);
                     L.bs[nb + off + i] = rs;
@@ -1000,14 +1111,16 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
             KC_SEC_BEGIN();
             // evaluate the batch, lane per child
             const int l2 = l - 2;
-            const bool has = lane < nb;
-            const int cu = has ? L.bu[lane] : 0;
-            const int cv = has ? L.bv[lane] : 0;
+            const int cu0 = lane < nb ? L.bu[lane] : 0;
+            const int cv0 = lane < nb ? L.bv[lane] : 0;
+            const bool has = lane < nb && KC_OK(cu0, s) && KC_OK(cv0, s);
+            const int cu = has ? cu0 : 0;
+            const int cv = has ? cv0 : 0;
             u32 cw[W];
             int cc = 0;
 #pragma unroll
             for (int w = 0; w < W; w++) {
-                u32 x = (has && w >= (cv >> 5)) ? (C[w] & L.A[cu * W + w] & L.A[cv * W + w] & gt_mask(cv, w)) : 0u;
+                u32 x = (has && w >= (cv >> 5)) ? (C[w] & L.A[cu * (W + KC_ROW_PAD) + w] & L.A[cv * (W + KC_ROW_PAD) + w] & gt_mask(cv, w)) : 0u;
                 cw[w] = x;
                 cc += __popc(x);
             }
@@ -1059,18 +1172,21 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
             } else if (l2 == 2) {
                 if (cc >= 2) {
                     u64 ec = 0, zs = 0;
+                    u32 rest[W];  // cw without the positions visited so far (all <= xp)
+#pragma unroll
+                    for (int w = 0; w < W; w++) rest[w] = cw[w];
 #pragma unroll (W <= 8 ? W : 1)
                     for (int w = 0; w < W; w++) {
-                        u32 x = cw[w];
-                        while (x) {
-                            int b = __ffs(x) - 1;
-                            x &= x - 1;
+                        while (rest[w]) {
+                            int b = __ffs(rest[w]) - 1;
+                            rest[w] &= rest[w] - 1;
                             const int xp = w * 32 + b;
                             acc.ops += 3u * (u32)(Ws - (xp >> 5));
                             u64 zin = 0;
 #pragma unroll
                             for (int w2 = 0; w2 < W; w2++) {
-                                u32 y = L.A[xp * W + w2] & cw[w2] & gt_mask(xp, w2);
+                                if (w2 < w) continue;
+                                u32 y = L.A[xp * (W + KC_ROW_PAD) + w2] & rest[w2];
                                 ec += __popc(y);
                                 if (SUM) {
                                     while (y) { int b2 = __ffs(y) - 1; y &= y - 1; zin += L.z[w2 * 32 + b2]; }
@@ -1096,7 +1212,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                                 x &= x - 1;
                                 const int xp = w * 32 + b;
                                 for (int w2 = 0; w2 < W; w2++) {
-                                    u32 y = L.A[xp * W + w2] & cw[w2] & gt_mask(xp, w2);
+                                    u32 y = L.A[xp * (W + KC_ROW_PAD) + w2] & cw[w2] & gt_mask(xp, w2);
                                     while (y) {
                                         int b2 = __ffs(y) - 1;
                                         y &= y - 1;
@@ -1114,11 +1230,11 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                 }
             } else {
                 bool closed = false;
-                if (!SUM && l2 == 3 && has && cc >= 3 && use_et) {
+                if (KC_PRECHECK && !SUM && l2 == 3 && has && cc >= 3 && use_et) {
                     // pre-check against the masks of this child's u: no vertex of C' has
                     // t_max non-neighbours even in the larger set Cu => C' is a t-plex
                     const int slot = L.bs[lane];
-                    const u32 *Bm = L.Bm + (d * 4 + slot) * W, *M1 = L.M1 + (d * 4 + slot) * W;
+                    const u32 *Bm = L.Bm + slot * W, *M1 = L.M1 + slot * W;
                     bool bad = false, any1 = false;
 #pragma unroll
                     for (int w = 0; w < W; w++) {
@@ -1138,7 +1254,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                                     bool nb = false;
 #pragma unroll
                                     for (int w2 = 0; w2 < W; w2++)
-                                        nb |= (cw[w2] & ~L.A[x * W + w2] & ~((w2 == (x >> 5)) ? (1u << (x & 31)) : 0u)) != 0u;
+                                        nb |= (cw[w2] & ~L.A[x * (W + KC_ROW_PAD) + w2] & ~((w2 == (x >> 5)) ? (1u << (x & 31)) : 0u)) != 0u;
                                     nonuni += nb;
                                 }
                             }
@@ -1152,7 +1268,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                         closed = true;
                     }
                 }
-                if (!closed && l2 == 3 && has && cc >= 3 && use_et && (!LIST || full)) {
+                if (!closed && l2 == 3 && has && cc >= 3 && cc <= KC_LANE_ET_MAX && use_et && (!LIST || full)) {
                     // l = 3 child: the t-plex test and the Alg. 6 count in this lane (a lane
                     // leaves the test at its first vertex of too small degree); SUM: the x^3
                     // coefficient of prod (1 + c x), c = z_f (universal) or z_a + z_b (pair)
@@ -1170,7 +1286,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                             int dg = 0;
 #pragma unroll
                             for (int w2 = 0; w2 < W; w2++)
-                                if (w2 >= w0) dg += __popc(L.A[x * W + w2] & cw[w2]);
+                                if (w2 >= w0) dg += __popc(L.A[x * (W + KC_ROW_PAD) + w2] & cw[w2]);
                             if (dg < cc - tmax) { plex = false; bits = 0; }
                             nuni += (dg == cc - 1);
                             if (SUM && plex) {
@@ -1180,7 +1296,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                                     int y = -1;
 #pragma unroll
                                     for (int w2 = 0; w2 < W; w2++) {
-                                        const u32 nb = (w2 >= w0) ? (cw[w2] & ~L.A[x * W + w2] &
+                                        const u32 nb = (w2 >= w0) ? (cw[w2] & ~L.A[x * (W + KC_ROW_PAD) + w2] &
                                                                      ~((w2 == (x >> 5)) ? (1u << (x & 31)) : 0u)) : 0u;
                                         if (y < 0 && nb) y = w2 * 32 + __ffs(nb) - 1;
                                     }
@@ -1206,7 +1322,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
             if (pb) {
                 const int slotc = __popc(pb & ((1u << lane) - 1));
                 const int dn = d + 1;
-                if (push) {
+                if (push && KC_OK(dn, a.D)) {
                     u32 *dst = L.childC + ((size_t)(dn * 32 + slotc)) * W;
 #pragma unroll
                     for (int w = 0; w < W; w++) dst[w] = cw[w];
@@ -1223,7 +1339,9 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
         if (phase == 2) {
             const int dn = d + 1;
             const int nx = L.nextc[dn];
-            if (nx < L.nchild[dn]) {
+            const int nch = L.nchild[dn];
+            __syncwarp();  // every lane has read nextc before lane 0 advances it
+            if (nx < nch) {
                 if (lane == 0) {
                     L.nextc[dn] = nx + 1;
                     L.slot[dn] = nx;
@@ -1254,7 +1372,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
 template <int W, int MODE>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK_DEFAULT, MinBlocks<W>::value)
 branch_kernel(Args a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    KC_DYN_SMEM(smem);
     constexpr bool SUM = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
     constexpr bool LIST = (MODE & MODE_LIST) != 0;
     const int lane = threadIdx.x & 31;
@@ -1262,12 +1380,14 @@ branch_kernel(Args a) {
     const Lay L = make_lay<W>(smem + (size_t)wib * a.warp_bytes, a.D, SUM);
     const bool use_et = !(a.flags & KC_NO_ET) && a.t_max >= 1;
     const bool use_rule1 = !(a.flags & KC_NO_RULE1);
-    const bool prof = a.prof != 0;
+    const bool prof = KC_SECTION_PROFILE && a.prof != 0;
     long long tsec = 0;
     Acc acc;
     reset_unit(acc);
     acc.nodes = 0; acc.et = 0; acc.status = 0; acc.ops = 0; acc.pairs = 0;
+#if KC_SECTION_PROFILE
     for (int i = 0; i < 6; i++) acc.sec[i] = 0;
+#endif
     WarpTotals wt;
     wt.q_total = 0; wt.q_csum = 0; wt.branches = 0; wt.cur_q = -1;
 
@@ -1303,6 +1423,7 @@ branch_kernel(Args a) {
         __syncwarp();
         reset_unit(acc);
         const bool full0 = LIST && (*(volatile unsigned long long *)&q.acc->written >= a.cap);
+        if (LIST && a.stop_full && __shfl_sync(0xffffffffu, (int)full0, 0)) break;
 
         if (l0 == 1) {
             acc.leaf += (lane == 0) ? (u64)s : 0ull;
@@ -1333,7 +1454,7 @@ branch_kernel(Args a) {
                     u64 zs = 0;
 #pragma unroll (W <= 8 ? W : 1)
                     for (int w = 0; w < W; w++) {
-                        u32 x = L.A[i * W + w] & gt_mask(i, w);
+                        u32 x = L.A[i * (W + KC_ROW_PAD) + w] & gt_mask(i, w);
                         c += __popc(x);
                         if (SUM) {
                             while (x) { int b = __ffs(x) - 1; x &= x - 1; zs += L.z[w * 32 + b]; }
@@ -1346,7 +1467,7 @@ branch_kernel(Args a) {
                         unsigned long long base = atomicAdd(&q.acc->written, (unsigned long long)c);
                         u32 idx = 0;
                         for (int w = 0; w < W; w++) {
-                            u32 x = L.A[i * W + w] & gt_mask(i, w);
+                            u32 x = L.A[i * (W + KC_ROW_PAD) + w] & gt_mask(i, w);
                             while (x) {
                                 int b = __ffs(x) - 1;
                                 x &= x - 1;
@@ -1359,6 +1480,15 @@ branch_kernel(Args a) {
                         }
                     }
                 }
+            } else if (l0 == 3 && (!LIST || full0)) {
+                // k = 5 counting: the triangles of g_e need no colours (Rules 1 and 2 only
+                // prune deeper branching), so the frame is counted in extraction order
+                if (lane < W) L.C0[lane] = lt_mask(s, lane);
+                __syncwarp();
+                if (lane == 0) acc.nodes++;
+                KC_SEC_BEGIN();
+                frame_l3_count<W, SUM>(L, L.C0, lane, acc, (int)a.t_max, use_et, Ws, P0);
+                KC_SEC_END(3);
             } else {
                 KC_SEC_BEGIN();
                 const int ncol_ok = colour_and_order<W>(L, s, lane);
@@ -1385,18 +1515,14 @@ branch_kernel(Args a) {
                     if (closed || limu <= 0) {
                         done = true;
                     } else {
-                        unsigned long long sl = 0, ib = 0;
-                        if (lane == 0) {
-                            sl = atomicAdd(a.slot_ctr, 1ull);
-                            ib = sl < a.slot_cap ? atomicAdd(a.item_ctr, (unsigned long long)limu) : ~0ull;
-                        }
+                        unsigned long long sl = 0;
+                        if (lane == 0) sl = atomicAdd(a.slot_ctr, 1ull);
                         sl = __shfl_sync(0xffffffffu, sl, 0);
-                        ib = __shfl_sync(0xffffffffu, ib, 0);
-                        if (sl < a.slot_cap && ib + (u64)limu <= a.item_cap) {
+                        if (sl < a.slot_cap) {
                             unsigned char *gs = a.slots + sl * (u64)slot_bytes<W>();
                             if (lane == 0) {
                                 SlotHdr h;
-                                h.e = e; h.s = (u32)s; h.qi = (u32)qi; h.pad = 0; h.P0 = P0; h.pad2 = 0;
+                                h.e = e; h.s = (u32)s; h.qi = (u32)qi; h.limu = (u32)limu; h.P0 = P0; h.pad2 = 0;
                                 *(SlotHdr *)gs = h;
                             }
                             u32 *gA = (u32 *)(gs + 32);
@@ -1404,11 +1530,10 @@ branch_kernel(Args a) {
                             uint16_t *gcol = (uint16_t *)(gvid + 32 * W);
                             uint16_t *glim = gcol + 32 * W;
                             u32 *gJ = (u32 *)((unsigned char *)glim + ((2u * (32u * W + 2) + 15u) & ~15u));
-                            for (int i = lane; i < s * W; i += 32) gA[i] = L.A[i];
+                            for (int i = lane; i < s * W; i += 32) gA[i] = L.A[(i / W) * (W + KC_ROW_PAD) + (i % W)];
                             for (int i = lane; i < s; i += 32) { gvid[i] = L.vid[i]; gcol[i] = L.col[i]; }
                             for (int i = lane; i < 32 * W + 2; i += 32) glim[i] = L.lim[i];
                             if (lane < W) { gJ[lane] = L.J[lane]; gJ[W + lane] = L.E[lane]; }
-                            for (int u = lane; u < limu; u += 32) a.items[ib + u] = (sl << 32) | (u64)u;
                             done = true;
                         }
                         // else: no room left, run the sub-branch here (below)
@@ -1422,63 +1547,85 @@ branch_kernel(Args a) {
     flush_query<MODE>(a, acc, wt, lane, prof);
 }
 
-// A12 work items of split sub-branches: (slot, u) -> the child edges (u, v) of the top
-// frame of that sub-branch and everything below them.
+// A12 split sub-branches: a block takes one published sub-branch (slot) at a time, loads
+// its frame once into shared memory, and its warps take the top-frame vertices u
+// (0 <= u < limu) from a block counter; each u runs the child edges (u, v) of the top
+// frame and everything below them.  Items of one slot are handed out in increasing u,
+// the costliest first, so the block's wait for its last warp is short.
+template <int W>
+struct ItemMinBlocks {
+    static constexpr int value = W <= 4 ? 6 : (W <= 8 ? KC_ITEM_MINB8 : (W <= 16 ? 2 : 1));
+};
+
 template <int W, int MODE>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK_DEFAULT, MinBlocks<W>::value)
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK_DEFAULT, ItemMinBlocks<W>::value)
 branch_items_kernel(Args a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    KC_DYN_SMEM(smem);
     constexpr bool SUM = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
+    constexpr int RS = W + KC_ROW_PAD;
+    __shared__ unsigned long long s_slot;
+    __shared__ int s_unext;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const Lay L = make_lay<W>(smem + (size_t)wib * a.warp_bytes, a.D, SUM);
-    const bool prof = a.prof != 0;
+    unsigned char *frame = smem;
+    const Lay L = make_lay<W>(smem + frame_bytes<W>(SUM) + (size_t)wib * a.warp_bytes, a.D, SUM, frame);
+    const bool prof = KC_SECTION_PROFILE && a.prof != 0;
     Acc acc;
     reset_unit(acc);
     acc.nodes = 0; acc.et = 0; acc.status = 0; acc.ops = 0; acc.pairs = 0;
+#if KC_SECTION_PROFILE
     for (int i = 0; i < 6; i++) acc.sec[i] = 0;
+#endif
     WarpTotals wt;
     wt.q_total = 0; wt.q_csum = 0; wt.branches = 0; wt.cur_q = -1;
-    const u64 n_items = *(volatile unsigned long long *)a.item_ctr;
-    long long cached = -1;
+    const u64 n_slots = min((u64)*(volatile unsigned long long *)a.slot_ctr, a.slot_cap);
     while (true) {
-        unsigned long long it = 0;
-        if (lane == 0) it = atomicAdd(a.item_next, 1ull);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= n_items || it >= a.item_cap) break;
-        const u64 item = a.items[it];
-        const u64 sl = item >> 32;
-        const int u = (int)(item & 0xFFFFFFFFull);
+        if (threadIdx.x == 0) {
+            s_slot = atomicAdd(a.slot_next, 1ull);
+            s_unext = 0;
+        }
+        __syncthreads();
+        const u64 sl = s_slot;
+        if (sl >= n_slots) break;
         const unsigned char *gs = a.slots + sl * (u64)slot_bytes<W>();
         const SlotHdr h = *(const SlotHdr *)gs;
-        const int qi = (int)h.qi;
-        if (qi != wt.cur_q) { flush_query<MODE>(a, acc, wt, lane, prof); wt.cur_q = qi; }
-        const QDesc &q = a.qs[qi];
-        const int s = (int)h.s;
-        const int l0 = (int)q.k - 2;
-        const int Ws = (s + 31) >> 5;
-        const long long t_start = clock64();
-        if ((long long)sl != cached) {
+        const int s = KC_OK(h.s, 32 * W + 1) ? (int)h.s : 0;
+        const int limu = KC_OK(h.limu, s + 1) ? (int)h.limu : 0;
+        {
             const u32 *gA = (const u32 *)(gs + 32);
             const u32 *gvid = gA + (32 * W) * W;
             const uint16_t *gcol = (const uint16_t *)(gvid + 32 * W);
             const uint16_t *glim = gcol + 32 * W;
             const u32 *gJ = (const u32 *)((const unsigned char *)glim + ((2u * (32u * W + 2) + 15u) & ~15u));
-            for (int i = lane; i < s * W; i += 32) L.A[i] = gA[i];
-            for (int i = lane; i < s; i += 32) {
-                L.vid[i] = gvid[i];
+            for (int i = threadIdx.x; i < s * W; i += blockDim.x) L.A[(i / W) * RS + (i % W)] = gA[i];
+            for (int i = threadIdx.x; i < s; i += blockDim.x) {
+                const u32 v = gvid[i];
+                L.vid[i] = v;
                 L.col[i] = gcol[i];
-                if (SUM) L.z[i] = zkey(gvid[i]);
+                if (SUM) L.z[i] = zkey(v);
             }
-            for (int i = lane; i < 32 * W + 2; i += 32) L.lim[i] = glim[i];
-            if (lane < W) { L.J[lane] = gJ[lane]; L.E[lane] = gJ[W + lane]; }
+            for (int i = threadIdx.x; i < 32 * W + 2; i += blockDim.x) L.lim[i] = glim[i];
+            if (threadIdx.x < W) { L.J[threadIdx.x] = gJ[threadIdx.x]; L.E[threadIdx.x] = gJ[W + threadIdx.x]; }
+        }
+        __syncthreads();
+        const int qi = (int)h.qi;
+        if (qi != wt.cur_q) { flush_query<MODE>(a, acc, wt, lane, prof); wt.cur_q = qi; }
+        const QDesc &q = a.qs[qi];
+        const int l0 = (int)q.k - 2;
+        const int Ws = (s + 31) >> 5;
+        while (true) {
+            int u = 0;
+            if (lane == 0) u = atomicAdd(&s_unext, 1);
+            u = __shfl_sync(0xffffffffu, u, 0);
+            if (u >= limu) break;
+            const long long t_start = clock64();
             if (lane == 0) { L.path[0] = q.eu[h.e]; L.path[1] = q.ev[h.e]; }
             __syncwarp();
-            cached = (long long)sl;
+            reset_unit(acc);
+            run_dfs<W, MODE>(L, a, q, s, l0, h.P0, lane, acc, Ws, u, u + 1, false, prof);
+            finish_unit<MODE>(q, h.e, acc, wt, lane, t_start);
         }
-        reset_unit(acc);
-        run_dfs<W, MODE>(L, a, q, s, l0, h.P0, lane, acc, Ws, u, u + 1, false, prof);
-        finish_unit<MODE>(q, h.e, acc, wt, lane, t_start);
+        __syncthreads();  // every warp is done with this frame before the next one loads
     }
     flush_query<MODE>(a, acc, wt, lane, prof);
 }
@@ -1505,20 +1652,33 @@ __global__ void binom_kernel(u128 *T) {
     }
 }
 
-std::vector<u128 *> g_tables;  // per device
+// binomial tables, one per device; created once under g_tables_mu (the library may
+// be entered from several host threads, e.g. a server's worker pool)
+constexpr int KC_MAX_DEVICES = 64;
+u128 *g_tables[KC_MAX_DEVICES] = {};
+std::mutex g_tables_mu;
 
+#ifndef KC_EMU  // host-side launch code (not part of a host emulation of the kernels)
 // launch geometry for a persistent kernel: (blocks, warps per block, shared bytes)
+// block_bytes: dynamic shared memory per block on top of warp_bytes per warp
 template <typename K>
-kc_status geometry(K kern, u32 warp_bytes, u64 work, const kc_run_cfg *cfg, u64 *blocks, int *wpb_out, size_t *smem_out) {
+kc_status geometry(K kern, u32 warp_bytes, u64 work, const kc_run_cfg *cfg, u64 *blocks, int *wpb_out, size_t *smem_out,
+                   u32 block_bytes = 0) {
     int wpb = WARPS_PER_BLOCK_DEFAULT;
-    size_t smem = (size_t)warp_bytes * wpb;
     int dev = 0, max_optin = 0, nsm = 0;
     KC_CUDA(cudaGetDevice(&dev));
     KC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     KC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    while (smem > (size_t)max_optin && wpb > 1) { wpb--; smem = (size_t)warp_bytes * wpb; }
-    if (smem > (size_t)max_optin) return KC_ERR_UNSUPPORTED;
-    KC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaFuncAttributes fa;
+    KC_CUDA(cudaFuncGetAttributes(&fa, kern));
+    const size_t dyn_max = (size_t)max_optin - fa.sharedSizeBytes;  // minus static __shared__
+    size_t smem = (size_t)block_bytes + (size_t)warp_bytes * wpb;
+    while (smem > dyn_max && wpb > 1) { wpb--; smem = (size_t)block_bytes + (size_t)warp_bytes * wpb; }
+    if (smem > dyn_max) return KC_ERR_UNSUPPORTED;
+    // the attribute is per kernel and process-wide: always the same value (the opt-in
+    // maximum), so launches of one kernel with different sizes from several host
+    // threads cannot invalidate each other's launch configuration
+    KC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max));
     int per_sm = 0;
     KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, smem));
     if (per_sm < 1) per_sm = 1;
@@ -1537,8 +1697,6 @@ kc_status geometry(K kern, u32 warp_bytes, u64 work, const kc_run_cfg *cfg, u64 
 struct SplitBufs {
     unsigned char *slots = nullptr;
     u64 slot_bytes_cap = 0;
-    u64 *items = nullptr;
-    u64 item_cap = 0;
 };
 
 template <int W, int MODE>
@@ -1567,26 +1725,16 @@ kc_status launch_class(const Args &a0, const std::vector<QDesc> &qs, const kc_ru
     a.slots = nullptr;
     if (nheavy && !(MODE & MODE_LIST)) {
         const u64 need_slots = nheavy * (u64)slot_bytes<W>();
-        const u64 need_items = nheavy * 32ull * W;
         if (sb->slot_bytes_cap < need_slots) {
             if (sb->slots) KC_CUDA(cudaFreeAsync(sb->slots, s));
             sb->slots = nullptr;
             KC_CUDA(cudaMallocAsync(&sb->slots, need_slots, s));
             sb->slot_bytes_cap = need_slots;
         }
-        if (sb->item_cap < need_items) {
-            if (sb->items) KC_CUDA(cudaFreeAsync(sb->items, s));
-            sb->items = nullptr;
-            KC_CUDA(cudaMallocAsync(&sb->items, need_items * sizeof(u64), s));
-            sb->item_cap = need_items;
-        }
         a.slots = sb->slots;
         a.slot_cap = nheavy;
-        a.items = sb->items;
-        a.item_cap = need_items;
         a.slot_ctr = d_ctr + 1;
-        a.item_ctr = d_ctr + 2;
-        a.item_next = d_ctr + 3;
+        a.slot_next = d_ctr + 2;
     }
     u64 blocks = 1;
     int wpb = 1;
@@ -1598,9 +1746,13 @@ kc_status launch_class(const Args &a0, const std::vector<QDesc> &qs, const kc_ru
     KC_CUDA(cudaGetLastError());
     if (a.slots) {
         // the item count is only known on the device: size the grid for a full machine
-        st = geometry(branch_items_kernel<W, MODE>, a.warp_bytes, ~0ull >> 8, cfg, &blocks, &wpb, &smem);
+        constexpr bool sum = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
+        Args ai = a;
+        ai.warp_bytes = lay_bytes<W>(D, sum, true);
+        st = geometry(branch_items_kernel<W, MODE>, ai.warp_bytes, ~0ull >> 8, cfg, &blocks, &wpb, &smem,
+                      frame_bytes<W>(sum));
         if (st != KC_OK) return st;
-        branch_items_kernel<W, MODE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
+        branch_items_kernel<W, MODE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(ai);
         kc_note_launch();
         KC_CUDA(cudaGetLastError());
     }
@@ -1621,12 +1773,15 @@ kc_status launch_mode(int W, const Args &a, const std::vector<QDesc> &qs, const 
     return KC_ERR_UNSUPPORTED;
 }
 
+#endif  // KC_EMU
 }  // namespace
+#ifndef KC_EMU
 
 kc_status kc_ensure_tables(cudaStream_t s) {
     int dev = 0;
     KC_CUDA(cudaGetDevice(&dev));
-    if ((int)g_tables.size() <= dev) g_tables.resize(dev + 1, nullptr);
+    if (dev < 0 || dev >= KC_MAX_DEVICES) return KC_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_tables_mu);
     if (!g_tables[dev]) {
         // keep stream-ordered scratch (split buffers, prepare temporaries) cached in the pool
         cudaMemPool_t pool;
@@ -1669,8 +1824,13 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
     a.flags = cfg->flags;
     a.d_out = cfg->d_out;
     a.cap = cfg->cap;
+    a.stop_full = cfg->list && cfg->stop_full ? 1u : 0u;
     a.binom = g_tables[dev];
-    a.prof = getenv("KC_PROFILE") ? 1u : 0u;
+    a.prof = (KC_SECTION_PROFILE && getenv("KC_PROFILE")) ? 1u : 0u;
+    if (a.prof) {
+        KC_CUDA(cudaMallocAsync(&a.l3hist, 16 * sizeof(unsigned long long), s));
+        KC_CUDA(cudaMemsetAsync(a.l3hist, 0, 16 * sizeof(unsigned long long), s));
+    }
     int mode = cfg->list ? MODE_LIST : ((cfg->flags & KC_CHECKSUM) ? MODE_CHECKSUM : 0);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1749,6 +1909,16 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
     cudaEventRecord(e1, s);
     if (st == KC_OK) KC_CUDA(cudaMemcpyAsync(h_acc, d_acc, sizeof(kc_dev_acc) * nq, cudaMemcpyDeviceToHost, s));
     cudaStreamSynchronize(s);
+#if KC_DEBUG_BOUNDS
+    {
+        unsigned long long dbg = 0, zero = 0;
+        if (cudaMemcpyFromSymbol(&dbg, g_kc_dbg, sizeof(dbg)) == cudaSuccess && dbg) {
+            fprintf(stderr, "[kclique] bounds check failed: line %llu index %llu bound %llu\n", dbg >> 40,
+                    (dbg >> 20) & 0xFFFFFull, dbg & 0xFFFFFull);
+            cudaMemcpyToSymbol(g_kc_dbg, &zero, sizeof(zero));
+        }
+    }
+#endif
     if (profile && st == KC_OK) {
         const char *names[6] = {"extract", "colour", "et(l>=4)", "l3-frames", "generate", "evaluate"};
         for (int i = 0; i < 6; i++) {
@@ -1756,7 +1926,14 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
             for (u32 j = 0; j < nq; j++) t += h_acc[j].sec[i];
             fprintf(stderr, "[kclique] section %-10s %.3e warp-cycles\n", names[i], (double)t);
         }
+        unsigned long long hh[16];
+        if (cudaMemcpy(hh, a.l3hist, sizeof(hh), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            const char *bn[7] = {"<=8", "<=16", "<=32", "<=64", "<=128", "<=256", ">256"};
+            for (int i = 0; i < 7; i++)
+                fprintf(stderr, "[kclique] l3 frames %-5s %12llu  %.3e warp-cycles\n", bn[i], hh[i], (double)hh[8 + i]);
+        }
     }
+    if (a.l3hist) cudaFreeAsync(a.l3hist, s);
     cudaEventElapsedTime(ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1765,7 +1942,6 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
     cudaFreeAsync(d_qstart, s);
     cudaFreeAsync(d_ctr, s);
     if (sb.slots) cudaFreeAsync(sb.slots, s);
-    if (sb.items) cudaFreeAsync(sb.items, s);
     cudaStreamSynchronize(s);
     if (st == KC_OK) {
         cudaError_t ce = cudaGetLastError();
@@ -1970,3 +2146,4 @@ kc_status kc_run_queries_in_scratch(const kc_query *qv, u32 nq, u32 t_max, u32 f
     KC_CUDA(cudaStreamSynchronize(s));
     return KC_OK;
 }
+#endif  // KC_EMU

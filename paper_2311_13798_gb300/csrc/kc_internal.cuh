@@ -81,6 +81,7 @@ struct kc_run_cfg {
     u32 warps_per_block;
     u32 blocks;
     int list;           // 1 = write cliques
+    int stop_full;      // list: end the pass once the buffer is full (totals then partial)
     u32 *d_out;
     u64 cap;
     u64 *d_edge_count;

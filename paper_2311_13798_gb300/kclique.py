@@ -32,6 +32,7 @@ KC_NO_ET = 0x1
 KC_NO_RULE2 = 0x2
 KC_CHECKSUM = 0x4
 KC_NO_RULE1 = 0x8
+KC_ROWS_ONLY = 0x10
 
 
 class KcParams(C.Structure):

@@ -5,7 +5,10 @@ Requests arrive at any time through ``submit``.  Two worker threads drive the GP
 * the query worker takes every count request that arrived while the previous batch
   was running and runs them as ONE ``kclique_count_batch`` launch per width class
   (continuous batching: the batch is whatever is waiting, up to ``max_batch``); list
-  requests run one by one between batches;
+  requests go to a small pool of list workers, each on its own CUDA stream, which write
+  the rows only (``KC_ROWS_ONLY``: the pass ends when the buffer is full); when a listing
+  was truncated its exact totals (count, checksum) are computed by a count entry that
+  joins the next batch, so a list query costs a short row pass plus a batched count;
 * the upload worker prepares newly uploaded graphs (``kclique_prepare``) on its own
   CUDA stream, so uploads overlap with counting on the device.
 
@@ -26,17 +29,18 @@ import collections
 import queue
 import threading
 import time
-from concurrent.futures import Future
+from concurrent.futures import Future, ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 
 @dataclass
 class Request:
-    kind: str                 # "count" | "list" | "upload"
+    kind: str                 # "count" | "list" | "upload" ("totals": internal, see _run_list)
     graph: str                # graph name (uploads: the name to register)
     k: int = 0
     cap: int = 0              # list: rows wanted
     csr: tuple | None = None  # upload: (row_ptr, col, n) host arrays
+    parent: object = None     # totals: (list request, its rows result)
     t_arrival: float = field(default_factory=time.perf_counter)
     future: Future = field(default_factory=Future)
 
@@ -55,7 +59,8 @@ class Result:
 
 
 class CudaBackend:
-    """libkclique calls on two CUDA streams (queries, uploads)."""
+    """libkclique calls on CUDA streams of their own: counts, uploads, and one stream
+    per list-worker thread."""
 
     def __init__(self, device: int = 0):
         import torch
@@ -64,8 +69,10 @@ class CudaBackend:
         self.K = K
         self.torch = torch
         torch.cuda.set_device(device)
+        self.device = device
         self.qstream = torch.cuda.Stream()
         self.ustream = torch.cuda.Stream()
+        self.tls = threading.local()
 
     def prepare(self, row_ptr, col, n):
         with self.torch.cuda.stream(self.ustream):
@@ -84,10 +91,14 @@ class CudaBackend:
         with self.torch.cuda.stream(self.qstream):
             return self.K.kclique_count_batch(handles, ks, stream=self.qstream, flags=self.K.KC_CHECKSUM)
 
-    def list(self, h, k, cap):
-        with self.torch.cuda.stream(self.qstream):
+    def list(self, h, k, cap, rows_only=False):
+        st = getattr(self.tls, "stream", None)
+        if st is None:
+            self.torch.cuda.set_device(self.device)
+            st = self.tls.stream = self.torch.cuda.Stream()
+        with self.torch.cuda.stream(st):
             out = self.torch.empty((max(cap, 1), k), dtype=self.torch.int32, device="cuda")
-            r = self.K.kclique_list(h, k, out, stream=self.qstream)
+            r = self.K.kclique_list(h, k, out, stream=st, flags=self.K.KC_ROWS_ONLY if rows_only else 0)
             return r, out[: r["written"]].cpu().numpy()
 
     def release(self, h):
@@ -95,7 +106,8 @@ class CudaBackend:
 
 
 class KCliqueServer:
-    def __init__(self, backend=None, hbm_budget_bytes: int = 120 << 30, max_batch: int = 512):
+    def __init__(self, backend=None, hbm_budget_bytes: int = 120 << 30, max_batch: int = 512,
+                 list_workers: int = 4):
         self.backend = backend or CudaBackend()
         self.budget = int(hbm_budget_bytes)
         self.max_batch = max_batch
@@ -112,9 +124,11 @@ class KCliqueServer:
         self.done: list[Result] = []
         self.batches: list[int] = []
         self.rejected = 0
+        self.lists_inflight = 0
         self.stop = False
         self.t_first = None
         self.t_last = None
+        self.list_pool = ThreadPoolExecutor(max_workers=max(1, list_workers))
         self.qt = threading.Thread(target=self._query_worker, daemon=True)
         self.ut = threading.Thread(target=self._upload_worker, daemon=True)
         self.qt.start()
@@ -144,12 +158,13 @@ class KCliqueServer:
             self.uq.put(req)
             return req.future
         with self.cv:
-            if req.graph not in self.graphs:
-                self._finish(req, Result(req.kind, req.graph, req.k, status="unknown graph"))
-                return req.future
-            self.waiting[req.graph] += 1
-            self.qq.append(req)
-            self.cv.notify()
+            known = req.graph in self.graphs
+            if known:
+                self.waiting[req.graph] += 1
+                self.qq.append(req)
+                self.cv.notify()
+        if not known:
+            self._finish(req, Result(req.kind, req.graph, req.k, status="unknown graph"))
         return req.future
 
     def close(self, timeout: float = 600.0):
@@ -159,13 +174,15 @@ class KCliqueServer:
         self.uq.put(None)
         self.qt.join(timeout)
         self.ut.join(timeout)
+        self.list_pool.shutdown(wait=True)
 
     # ------------------------------------------------------------ workers
     def _finish(self, req: Request, res: Result):
         t = time.perf_counter()
         res.latency_s = t - req.t_arrival
-        self.t_last = t
-        self.done.append(res)
+        with self.lock:
+            self.t_last = t
+            self.done.append(res)
         req.future.set_result(res)
 
     def _evict_for(self, need: int) -> bool:
@@ -219,17 +236,20 @@ class KCliqueServer:
     def _query_worker(self):
         while True:
             with self.cv:
-                while not self.qq and not self.stop:
+                while not self.qq and not (self.stop and self.lists_inflight == 0):
                     self.cv.wait()
-                if not self.qq and self.stop:
+                if not self.qq:  # stopping, and no listing can still add a totals entry
                     return
                 batch, lists = [], []
                 while self.qq and len(batch) < self.max_batch:
                     r = self.qq.popleft()
-                    (lists if r.kind == "list" else batch).append(r)
+                    (lists if r.kind == "list" else batch).append(r)  # count and totals batch
                 handles = {r.graph: self.graphs[r.graph] for r in batch + lists}
                 for g in handles:
                     self.lru.move_to_end(g)
+                self.lists_inflight += len(lists)
+            for r in lists:
+                self.list_pool.submit(self._run_list, r, handles[r.graph])
             if batch:
                 self.batches.append(len(batch))
                 try:
@@ -239,18 +259,37 @@ class KCliqueServer:
                 except Exception as e:
                     outs = [Result("count", r.graph, r.k, status=f"error: {e}") for r in batch]
                 for r, o in zip(batch, outs):
-                    self._finish(r, o)
-            for r in lists:
-                try:
-                    x, rows = self.backend.list(handles[r.graph], r.k, r.cap)
-                    o = Result("list", r.graph, r.k, count=x["count"], checksum=x["checksum"],
-                               written=x["written"], rows=rows)
-                except Exception as e:
-                    o = Result("list", r.graph, r.k, status=f"error: {e}")
-                self._finish(r, o)
+                    if r.kind == "totals":  # completes a truncated listing
+                        req, lo = r.parent
+                        lo.count, lo.checksum = o.count, o.checksum
+                        if o.status != "ok":
+                            lo.status = o.status
+                        self._finish(req, lo)
+                    else:
+                        self._finish(r, o)
             with self.cv:
-                for r in batch + lists:
+                for r in batch:
                     self.waiting[r.graph] -= 1
+
+    def _run_list(self, r: Request, h):
+        try:
+            x, rows = self.backend.list(h, r.k, r.cap, rows_only=True)
+            o = Result("list", r.graph, r.k, count=x["count"], checksum=x["checksum"],
+                       written=x["written"], rows=rows)
+            truncated = bool(x.get("truncated"))
+        except Exception as e:
+            o = Result("list", r.graph, r.k, status=f"error: {e}")
+            truncated = False
+        with self.cv:
+            if truncated:  # the totals join the next count batch; the graph stays held
+                self.waiting[r.graph] += 1
+                self.qq.append(Request("totals", r.graph, k=r.k, t_arrival=r.t_arrival, parent=(r, o)))
+                self.cv.notify()
+            self.waiting[r.graph] -= 1
+            self.lists_inflight -= 1
+            self.cv.notify_all()
+        if not truncated:
+            self._finish(r, o)
 
     # ------------------------------------------------------------ statistics
     def stats(self) -> dict:

@@ -49,3 +49,14 @@ def test_binding_rejects_bad_arguments_without_gpu():
     assert lib.kclique_count(None, 4, None, None, ctypes.byref(r)) == kclique.KC_ERR_INVALID_ARG
     h = ctypes.c_void_p()
     assert lib.kclique_prepare(None, None, 0, 0, 0, None, ctypes.byref(h)) == kclique.KC_ERR_INVALID_ARG
+
+
+def test_flag_and_limit_constants_match_the_header():
+    """Every numeric #define of include/kclique.h has the same value in the binding."""
+    import re
+    from paper_2311_13798_gb300 import kclique
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "kclique.h")).read()
+    found = re.findall(r"#define (KC_[A-Z0-9_]+) (0x[0-9a-fA-F]+|\d+)u?\b", hdr)
+    assert len(found) >= 7
+    for name, val in found:
+        assert getattr(kclique, name) == int(val, 0), name

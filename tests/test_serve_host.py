@@ -35,10 +35,14 @@ class FakeBackend:
         time.sleep(self.delay)
         return [dict(O.count(h["g"], k)) for h, k in zip(hs, ks)]
 
-    def list(self, h, k, cap):
+    def list(self, h, k, cap, rows_only=False):
         rows = O.list_cliques(h["g"], k)
         r = O.count(h["g"], k)
-        return {"count": r["count"], "checksum": r["checksum"], "written": min(cap, len(rows))}, rows[:cap]
+        trunc = len(rows) > cap
+        if rows_only and len(rows) >= cap:  # the library stops at a full buffer, totals unknown
+            return {"count": 0, "checksum": 0, "written": cap, "truncated": True}, rows[:cap]
+        return {"count": r["count"], "checksum": r["checksum"], "written": min(cap, len(rows)),
+                "truncated": trunc}, rows[:cap]
 
     def release(self, h):
         self.released.append(h)
@@ -91,3 +95,26 @@ def test_upload_admission_and_lru_eviction():
     assert r.count == O.count(small, 3)["count"]
     srv.close()
     assert srv.stats()["rejected"] == 1
+
+
+def test_truncated_listings_get_their_totals_from_the_count_batch():
+    be = FakeBackend()
+    srv = KCliqueServer(be, hbm_budget_bytes=1 << 30)
+    g = G.gnp(60, 0.4, seed=5)
+    srv.register("g", *_csr(g))
+    futs = [srv.submit(Request("list", "g", k=k, cap=cap)) for k in (3, 4) for cap in (1, 7, 10**6)]
+    futs += [srv.submit(Request("count", "g", k=3))]
+    res = [f.result(timeout=60) for f in futs]
+    srv.close()
+    i = 0
+    for k in (3, 4):
+        want = O.count(g, k)
+        n = len(O.list_cliques(g, k))
+        for cap in (1, 7, 10**6):
+            r = res[i]
+            i += 1
+            assert r.status == "ok" and (r.count, r.checksum) == (want["count"], want["checksum"])
+            assert r.written == min(cap, n) and len(r.rows) == r.written
+    assert res[-1].count == O.count(g, 3)["count"]
+    # 4 truncated listings (caps 1 and 7) went through the count batches, plus the count
+    assert sum(be.calls) == 5
