@@ -56,6 +56,8 @@ def parse(argv=None):
                          "measurements (separate JSON lines); probe: one count on a Chung-Lu graph sized "
                          "by the --probe-* flags, the small case for profiler captures (not a bench value)")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--serve-split-min", type=int, default=64,
+                    help="serve: |VSet| from which the server's batches split k >= 7 sub-branches (0: library default)")
     ap.add_argument("--probe-n", type=int, default=1_000_000)
     ap.add_argument("--probe-wmax", type=float, default=3000.0)
     ap.add_argument("--probe-k", type=int, default=7)
@@ -280,7 +282,7 @@ def run_serve(args):
     cap = 1024
 
     def replay_server():
-        srv = KCliqueServer(CudaBackend(), hbm_budget_bytes=120 << 30)
+        srv = KCliqueServer(CudaBackend(split_min=args.serve_split_min), hbm_budget_bytes=120 << 30)
         for j, g in enumerate(base):
             srv.register(f"g{j}", g.row_ptr, g.col, g.n)
         torch.cuda.synchronize()
@@ -341,10 +343,12 @@ def run_serve(args):
     line = {"metric": "served k-clique queries/s (continuous batching)", "workload": "serve",
             "value": st_srv["throughput_qps"], "unit": "queries/s", "p50_s": st_srv["p50_s"],
             "p99_s": st_srv["p99_s"], "batches": st_srv["batches"], "mean_batch": st_srv["mean_batch"],
-            "rejected": st_srv["rejected"], "one_query_per_launch": st_fifo,
+            "rejected": st_srv["rejected"], "span_s": st_srv["span_s"], "busy_s": st_srv["busy_s"],
+            "max_batch_seen": st_srv["max_batch_seen"], "one_query_per_launch": st_fifo,
             "speedup": st_srv["throughput_qps"] / st_fifo["throughput_qps"], "results_identical": same,
             "errors": errors[:5],
-            "config": {"arrivals": n_arr, "rate_qps": 2000, "resident": "4 x G(2000,0.01) seeds 0-3 + "
+            "config": {"arrivals": n_arr, "rate_qps": 2000, "split_min": args.serve_split_min,
+                       "resident": "4 x G(2000,0.01) seeds 0-3 + "
                        "4 x Chung-Lu n=1e5 wmax=2000 seeds 0-3", "k": "U{4..10}", "mix": "35% count, 35% list "
                        "(cap 1024 rows), 30% upload of 4x250 SBM with one 2-plex block", "hbm_budget_GB": 120}}
     print(json.dumps(line), flush=True)

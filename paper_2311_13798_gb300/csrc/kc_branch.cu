@@ -38,7 +38,7 @@
 #define KC_SCAN_RATIO 4
 #endif
 #ifndef KC_ITEM_MINB8  // resident blocks per SM asked of the compiler, item kernel, W = 8
-#define KC_ITEM_MINB8 5   // (5: 96 registers; 4.5 % faster than 4 on the power-law k = 7 run)
+#define KC_ITEM_MINB8 6   // (6: 80 registers; 8 % faster than 4 on the power-law k = 7 run)
 #endif
 #ifndef KC_LANE_ET_MAX  // l = 3 children up to this size get the in-lane plex test; larger ones
 #define KC_LANE_ET_MAX 1024  // go to the warp routine, which tests them too
@@ -1547,11 +1547,12 @@ branch_kernel(Args a) {
     flush_query<MODE>(a, acc, wt, lane, prof);
 }
 
-// A12 split sub-branches: a block takes one published sub-branch (slot) at a time, loads
-// its frame once into shared memory, and its warps take the top-frame vertices u
-// (0 <= u < limu) from a block counter; each u runs the child edges (u, v) of the top
-// frame and everything below them.  Items of one slot are handed out in increasing u,
-// the costliest first, so the block's wait for its last warp is short.
+// A12 split sub-branches: a block takes one work unit at a time -- a published sub-branch
+// (slot), or with few slots a stride class of one slot's top-frame vertices -- loads the
+// slot's frame into shared memory unless it holds it already, and its warps take the
+// unit's vertices u from a block counter; each u runs the child edges (u, v) of the top
+// frame and everything below them.  Vertices are handed out in increasing u, the
+// costliest first, so the block's wait for its last warp is short.
 template <int W>
 struct ItemMinBlocks {
     static constexpr int value = W <= 4 ? 6 : (W <= 8 ? KC_ITEM_MINB8 : (W <= 16 ? 2 : 1));
@@ -1579,19 +1580,27 @@ branch_items_kernel(Args a) {
     WarpTotals wt;
     wt.q_total = 0; wt.q_csum = 0; wt.branches = 0; wt.cur_q = -1;
     const u64 n_slots = min((u64)*(volatile unsigned long long *)a.slot_ctr, a.slot_cap);
+    // with few slots, several blocks share one: a work unit is (slot, c), c < cps, and takes
+    // the vertices u = c, c + cps, c + 2 cps, ... (a mix of costly low u and cheap high u)
+    const u64 want_units = 8ull * gridDim.x;
+    const u32 cps = n_slots >= want_units ? 1u : (u32)min((u64)((want_units + n_slots - 1) / (n_slots ? n_slots : 1)), (u64)64);
+    const u64 n_units = n_slots * cps;
+    long long loaded = -1;  // slot whose frame this block holds
     while (true) {
         if (threadIdx.x == 0) {
             s_slot = atomicAdd(a.slot_next, 1ull);
             s_unext = 0;
         }
         __syncthreads();
-        const u64 sl = s_slot;
-        if (sl >= n_slots) break;
+        const u64 unit = s_slot;
+        if (unit >= n_units) break;
+        const u64 sl = unit / cps;
+        const u32 c0 = (u32)(unit % cps);
         const unsigned char *gs = a.slots + sl * (u64)slot_bytes<W>();
         const SlotHdr h = *(const SlotHdr *)gs;
         const int s = KC_OK(h.s, 32 * W + 1) ? (int)h.s : 0;
         const int limu = KC_OK(h.limu, s + 1) ? (int)h.limu : 0;
-        {
+        if ((long long)sl != loaded) {
             const u32 *gA = (const u32 *)(gs + 32);
             const u32 *gvid = gA + (32 * W) * W;
             const uint16_t *gcol = (const uint16_t *)(gvid + 32 * W);
@@ -1606,6 +1615,7 @@ branch_items_kernel(Args a) {
             }
             for (int i = threadIdx.x; i < 32 * W + 2; i += blockDim.x) L.lim[i] = glim[i];
             if (threadIdx.x < W) { L.J[threadIdx.x] = gJ[threadIdx.x]; L.E[threadIdx.x] = gJ[W + threadIdx.x]; }
+            loaded = (long long)sl;
         }
         __syncthreads();
         const int qi = (int)h.qi;
@@ -1614,10 +1624,12 @@ branch_items_kernel(Args a) {
         const int l0 = (int)q.k - 2;
         const int Ws = (s + 31) >> 5;
         while (true) {
-            int u = 0;
-            if (lane == 0) u = atomicAdd(&s_unext, 1);
-            u = __shfl_sync(0xffffffffu, u, 0);
-            if (u >= limu) break;
+            int j = 0;
+            if (lane == 0) j = atomicAdd(&s_unext, 1);
+            j = __shfl_sync(0xffffffffu, j, 0);
+            const long long uu = (long long)c0 + (long long)cps * j;
+            if (uu >= limu) break;
+            const int u = (int)uu;
             const long long t_start = clock64();
             if (lane == 0) { L.path[0] = q.eu[h.e]; L.path[1] = q.ev[h.e]; }
             __syncwarp();

@@ -549,7 +549,8 @@ __global__ void retire_frontier_kernel(const u32 *__restrict__ F, u32 nf, uint8_
 // rounds separated by a software grid barrier.  Data written by other blocks inside the
 // launch is read with volatile loads (bypassing the non-coherent L1).
 struct PeelState {
-    u32 ctr[4];        // [0] alive after compaction, [1] frontier size, [2] least support, [3] next frontier
+    u32 ctr[4];        // [0] alive after compaction, [1] frontier size, [2] least support, [3] unused
+    u32 cnt[3];        // next-frontier sizes, rotating by round (round r writes cnt[r % 3])
     unsigned bar[2];   // barrier arrivals, generation
     unsigned status;   // KC_DEV_ERR_* bits
     u32 rounds;
@@ -584,6 +585,12 @@ __device__ __forceinline__ void grid_sync(PeelState *ps) {
 __device__ __forceinline__ u32 vld(const u32 *p) { return *(const volatile u32 *)p; }
 __device__ __forceinline__ uint8_t vld8(const uint8_t *p) { return *(const volatile uint8_t *)p; }
 
+// Rounds take two grid barriers: (A) retire the previous frontier, mark the current one
+// and clear the counter of the round after next | barrier | (B) remove the current
+// frontier's triangles, collecting the next frontier | barrier.  The frontier buffer of
+// round r - 1 is retired in (A) of round r and is then free for round r's next frontier.
+// The next-frontier counters rotate over three slots, so a slot is cleared two barriers
+// after every thread last read it.
 __global__ void __launch_bounds__(256) peel_persistent_kernel(u64 m, const u64 *__restrict__ inc_ptr,
                                                               const u64 *__restrict__ inc, u32 *sup, uint8_t *st,
                                                               u32 *level, u32 *round, u32 *alive, u32 *alive2,
@@ -592,12 +599,15 @@ __global__ void __launch_bounds__(256) peel_persistent_kernel(u64 m, const u64 *
     const u64 nthr = (u64)gridDim.x * blockDim.x;
     const u64 warp = tid >> 5, nwarps = nthr >> 5;
     const int lane = threadIdx.x & 31;
-    u32 lvl = 0, r = 0, nf = 0;
+    u32 lvl = 0, r = 0, nf = 0, nfp = 0;
+    u32 *Fp = Fn;  // previous frontier (to retire); its buffer takes the next frontier
     u64 nalive = m;
     for (u64 i = tid; i < m; i += nthr) alive[i] = (u32)i;
     grid_sync(ps);
     while (!(*(volatile unsigned *)&ps->status & KC_DEV_ERR_TIMEOUT)) {
         if (nf == 0) {
+            for (u64 i = tid; i < nfp; i += nthr) st[vld(&Fp[i])] = 2;
+            nfp = 0;
             if (nalive == 0) break;
             if (tid == 0) { ps->ctr[0] = 0; ps->ctr[2] = 0xFFFFFFFFu; }
             grid_sync(ps);
@@ -627,14 +637,19 @@ __global__ void __launch_bounds__(256) peel_persistent_kernel(u64 m, const u64 *
                 break;
             }
         }
+        // (A)
+        for (u64 i = tid; i < nfp; i += nthr) st[vld(&Fp[i])] = 2;
         for (u64 i = tid; i < nf; i += nthr) {
             const u32 e = vld(&F[i]);
             st[e] = 1;
             level[e] = lvl;
             round[e] = r;
         }
-        if (tid == 0) ps->ctr[3] = 0;
+        if (tid == 0) ps->cnt[(r + 1) % 3] = 0;
         grid_sync(ps);
+        // (B): the next frontier goes to Fp's buffer (retired above)
+        u32 *const Fnext = Fp;
+        u32 *const cnt = &ps->cnt[r % 3];
         for (u64 i = warp; i < nf; i += nwarps) {
             const u32 e = vld(&F[i]);
             for (u64 p = inc_ptr[e] + lane; p < inc_ptr[e + 1]; p += 32) {
@@ -643,16 +658,16 @@ __global__ void __launch_bounds__(256) peel_persistent_kernel(u64 m, const u64 *
                 const uint8_t s1 = vld8(&st[e1]), s2 = vld8(&st[e2]);
                 if (s1 == 2 || s2 == 2) continue;                       // destroyed in an earlier round
                 if ((s1 == 1 && e1 < e) || (s2 == 1 && e2 < e)) continue;  // another frontier edge owns it
-                if (s1 == 0) { u32 old = atomicSub(&sup[e1], 1u); if (old == lvl + 1) Fn[atomicAdd(&ps->ctr[3], 1u)] = e1; }
-                if (s2 == 0) { u32 old = atomicSub(&sup[e2], 1u); if (old == lvl + 1) Fn[atomicAdd(&ps->ctr[3], 1u)] = e2; }
+                if (s1 == 0) { u32 old = atomicSub(&sup[e1], 1u); if (old == lvl + 1) Fnext[atomicAdd(cnt, 1u)] = e1; }
+                if (s2 == 0) { u32 old = atomicSub(&sup[e2], 1u); if (old == lvl + 1) Fnext[atomicAdd(cnt, 1u)] = e2; }
             }
         }
         grid_sync(ps);
-        for (u64 i = tid; i < nf; i += nthr) st[vld(&F[i])] = 2;
-        nf = vld(&ps->ctr[3]);
-        u32 *t = F; F = Fn; Fn = t;
+        nfp = nf;
+        nf = vld(cnt);
+        Fp = F;
+        F = Fnext;
         r++;
-        grid_sync(ps);  // retired, and everyone has read ctr[3]
     }
     if (tid == 0) ps->rounds = r;
 }
@@ -934,7 +949,9 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
             const u64 *incp = inc_ptr, *incc = inc;
             void *kargs[] = {(void *)&m, (void *)&incp, (void *)&incc, (void *)&sup, (void *)&st, (void *)&lvl_p,
                              (void *)&rnd_p, (void *)&alive, (void *)&alive2, (void *)&F, (void *)&Fn, (void *)&ps};
-            const unsigned grid = (unsigned)std::min<u64>((u64)nsm * per_sm, kc_div_up(m, 256));
+            // few blocks: a round's work is small next to its two grid barriers, whose cost
+            // grows with the number of arriving blocks
+            const unsigned grid = (unsigned)std::min<u64>((u64)nsm * std::min(per_sm, 2), kc_div_up(m, 256));
             KC_CUDA(cudaLaunchCooperativeKernel((void *)peel_persistent_kernel, dim3(grid), dim3(256), kargs, 0, s));
             kc_note_launch();
             PeelState h;

@@ -62,7 +62,7 @@ class CudaBackend:
     """libkclique calls on CUDA streams of their own: counts, uploads, and one stream
     per list-worker thread."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, split_min: int = 64):
         import torch
 
         from . import kclique as K
@@ -70,6 +70,9 @@ class CudaBackend:
         self.torch = torch
         torch.cuda.set_device(device)
         self.device = device
+        # |VSet| from which the batches split k >= 7 sub-branches (0: the library's default);
+        # on the serving trace 64 balanced the batches better than the default 128
+        self.split_min = int(split_min)
         self.qstream = torch.cuda.Stream()
         self.ustream = torch.cuda.Stream()
         self.tls = threading.local()
@@ -89,7 +92,8 @@ class CudaBackend:
 
     def count_batch(self, handles, ks):
         with self.torch.cuda.stream(self.qstream):
-            return self.K.kclique_count_batch(handles, ks, stream=self.qstream, flags=self.K.KC_CHECKSUM)
+            return self.K.kclique_count_batch(handles, ks, stream=self.qstream, flags=self.K.KC_CHECKSUM,
+                                              split_min=self.split_min)
 
     def list(self, h, k, cap, rows_only=False):
         st = getattr(self.tls, "stream", None)
@@ -125,6 +129,7 @@ class KCliqueServer:
         self.batches: list[int] = []
         self.rejected = 0
         self.lists_inflight = 0
+        self.busy = {"count_batch": 0.0, "list": 0.0, "upload": 0.0}  # seconds inside backend calls
         self.stop = False
         self.t_first = None
         self.t_last = None
@@ -216,12 +221,14 @@ class KCliqueServer:
                 self.rejected += 1
                 self._finish(req, Result("upload", req.graph, 0, status="rejected: HBM budget"))
                 continue
+            t0 = time.perf_counter()
             try:
                 h = self.backend.prepare(rp, col, n)
                 status = "ok"
             except Exception as e:  # surfaced to the client, the server keeps running
                 h, status = None, f"error: {e}"
             with self.cv:
+                self.busy["upload"] += time.perf_counter() - t0
                 self.reserved -= need
                 if h is not None:
                     old = self.graphs.get(req.graph)
@@ -252,12 +259,14 @@ class KCliqueServer:
                 self.list_pool.submit(self._run_list, r, handles[r.graph])
             if batch:
                 self.batches.append(len(batch))
+                t0 = time.perf_counter()
                 try:
                     res = self.backend.count_batch([handles[r.graph] for r in batch], [r.k for r in batch])
                     outs = [Result("count", r.graph, r.k, count=x["count"], checksum=x["checksum"])
                             for r, x in zip(batch, res)]
                 except Exception as e:
                     outs = [Result("count", r.graph, r.k, status=f"error: {e}") for r in batch]
+                self.busy["count_batch"] += time.perf_counter() - t0
                 for r, o in zip(batch, outs):
                     if r.kind == "totals":  # completes a truncated listing
                         req, lo = r.parent
@@ -272,6 +281,7 @@ class KCliqueServer:
                     self.waiting[r.graph] -= 1
 
     def _run_list(self, r: Request, h):
+        t0 = time.perf_counter()
         try:
             x, rows = self.backend.list(h, r.k, r.cap, rows_only=True)
             o = Result("list", r.graph, r.k, count=x["count"], checksum=x["checksum"],
@@ -281,6 +291,7 @@ class KCliqueServer:
             o = Result("list", r.graph, r.k, status=f"error: {e}")
             truncated = False
         with self.cv:
+            self.busy["list"] += time.perf_counter() - t0
             if truncated:  # the totals join the next count batch; the graph stays held
                 self.waiting[r.graph] += 1
                 self.qq.append(Request("totals", r.graph, k=r.k, t_arrival=r.t_arrival, parent=(r, o)))
@@ -304,4 +315,5 @@ class KCliqueServer:
         return {"queries": nq, "uploads": sum(1 for r in self.done if r.kind == "upload"),
                 "rejected": self.rejected, "p50_s": pct(50), "p99_s": pct(99),
                 "throughput_qps": nq / span if span else None, "batches": len(self.batches),
-                "mean_batch": (sum(self.batches) / len(self.batches)) if self.batches else 0.0}
+                "mean_batch": (sum(self.batches) / len(self.batches)) if self.batches else 0.0,
+                "span_s": span, "busy_s": dict(self.busy), "max_batch_seen": max(self.batches, default=0)}

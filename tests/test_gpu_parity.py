@@ -165,6 +165,56 @@ def test_list_truncation_keeps_full_count(cache):
     assert len(rows) == cap and rows <= ref
 
 
+def test_rows_only_listing(cache):
+    """KC_ROWS_ONLY: a full buffer ends the pass with KC_TRUNCATED and no totals; a buffer
+    that holds every clique gives the exact totals as a normal listing does."""
+    K = kc()
+    g, cg, h = get(cache, "gnp120_dense")
+    k = 5
+    want = O.count(cg, k)
+    ref = set(map(tuple, O.list_cliques(cg, k).astype(np.int64).tolist()))
+    cap = want["count"] // 5
+    out = torch.zeros((cap, k), dtype=torch.int32, device="cuda")
+    got = K.kclique_list(h, k, out, flags=K.KC_ROWS_ONLY)
+    assert got["truncated"] and got["written"] == cap and got["count"] == 0 and got["checksum"] == 0
+    rows = set(map(tuple, out.cpu().numpy().astype(np.int64).tolist()))
+    assert len(rows) == cap and rows <= ref
+    out = torch.zeros((want["count"] + 7, k), dtype=torch.int32, device="cuda")
+    got = K.kclique_list(h, k, out, flags=K.KC_ROWS_ONLY)
+    assert not got["truncated"] and (got["count"], got["checksum"]) == (want["count"], want["checksum"])
+    assert set(map(tuple, out[: got["written"]].cpu().numpy().astype(np.int64).tolist())) == ref
+
+
+def test_concurrent_listings_from_host_threads(cache):
+    """Listings and counts issued at once from several host threads, each on its own
+    stream (the server's list workers), give the same results as alone."""
+    import concurrent.futures as cf
+    K = kc()
+    names = ["gnp120_dense", "chung_lu", "sbm", "two_plex"]
+    want = {}
+    for name in names:
+        g, cg, h = get(cache, name)
+        for k in (4, 5, 6):
+            want[(name, k)] = O.count(cg, k)
+
+    def job(name, k, cap):
+        torch.cuda.set_device(0)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            h = get(cache, name)[2]
+            out = torch.empty((cap, k), dtype=torch.int32, device="cuda")
+            r = K.kclique_list(h, k, out, stream=st)
+            c = K.kclique_count(h, k, stream=st, flags=K.KC_CHECKSUM)
+        return name, k, r, c
+
+    jobs = [(n, k, cap) for n in names for k in (4, 5, 6) for cap in (1, 1000)]
+    with cf.ThreadPoolExecutor(6) as ex:
+        for name, k, r, c in ex.map(lambda j: job(*j), jobs * 2):
+            w = want[(name, k)]
+            assert (r["count"], r["checksum"]) == (w["count"], w["checksum"]), (name, k)
+            assert (c["count"], c["checksum"]) == (w["count"], w["checksum"]), (name, k)
+
+
 def test_per_edge_counts(cache):
     for name in ("chung_lu", "sbm", "gnp120_dense"):
         g, cg, h = get(cache, name)
