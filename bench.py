@@ -56,13 +56,15 @@ def parse(argv=None):
                          "measurements (separate JSON lines); probe: one count on a Chung-Lu graph sized "
                          "by the --probe-* flags, the small case for profiler captures (not a bench value)")
     ap.add_argument("--batch-graphs", type=int, default=4096)
-    ap.add_argument("--serve-split-min", type=int, default=64,
+    ap.add_argument("--serve-split-min", type=int, default=0,
                     help="serve: |VSet| from which the server's batches split k >= 7 sub-branches (0: library default)")
     ap.add_argument("--probe-n", type=int, default=1_000_000)
     ap.add_argument("--probe-wmax", type=float, default=3000.0)
     ap.add_argument("--probe-k", type=int, default=7)
     ap.add_argument("--probe-checksum", action="store_true")
     ap.add_argument("--probe-tickets", default="", help="b:e -- count only tickets [b, e) (a shard)")
+    ap.add_argument("--probe-split-min", default="0",
+                    help="comma list of |VSet| split thresholds to time in turn (0: the library default)")
     return ap.parse_args(argv)
 
 
@@ -369,13 +371,14 @@ def run_probe(args):
     h = K.kclique_prepare(rp, col, g.n)
     flags = K.KC_CHECKSUM if args.probe_checksum else 0
     tb, te = (int(x) for x in args.probe_tickets.split(":")) if args.probe_tickets else (0, 0)
-    r = K.kclique_count(h, args.probe_k, flags=flags, ticket_begin=tb, ticket_end=te)
     info = K.kclique_info(h)
-    print(json.dumps({"workload": "probe", "n": g.n, "m": g.m, "w_max": args.probe_wmax, "tau": info["tau"],
-                      "k": args.probe_k, "tickets": [tb, te], "count": str(r["count"]),
-                      "checksum": str(r["checksum"]),
-                      "ms_branch": r["ms_branch"], "word_ops": r["word_ops"], "nodes": r["nodes"],
-                      "et_hits": r["et_hits"], "kernel_rev": K.kclique_kernel_rev()}), flush=True)
+    for sm in (int(x) for x in args.probe_split_min.split(",")):
+        r = K.kclique_count(h, args.probe_k, flags=flags, ticket_begin=tb, ticket_end=te, split_min=sm)
+        print(json.dumps({"workload": "probe", "n": g.n, "m": g.m, "w_max": args.probe_wmax, "tau": info["tau"],
+                          "k": args.probe_k, "tickets": [tb, te], "split_min": sm, "count": str(r["count"]),
+                          "checksum": str(r["checksum"]),
+                          "ms_branch": r["ms_branch"], "word_ops": r["word_ops"], "nodes": r["nodes"],
+                          "et_hits": r["et_hits"], "kernel_rev": K.kclique_kernel_rev()}), flush=True)
 
 
 def main(argv=None):

@@ -86,7 +86,7 @@ typedef struct {
     uint64_t *d_edge_checksum; /* optional device [m]: their checksum */
     uint64_t *d_edge_cycles;   /* optional device [m]: SM clock cycles the warps spent on e's sub-branch */
     uint32_t split_min;        /* k >= 7: sub-branches with |VSet| >= split_min are split across warps,
-                                  one work item per top-frame vertex (0 = 128; 0xFFFFFFFF = never) */
+                                  one work item per top-frame vertex (0 = 64; 0xFFFFFFFF = never) */
     uint32_t pad;
     uint64_t ticket_begin;     /* run only the top-level edges [ticket_begin, ticket_end) of the order by */
     uint64_t ticket_end;       /* |VSet| descending (0, 0 = all): a shard for one of several GPUs */

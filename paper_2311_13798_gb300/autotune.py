@@ -20,7 +20,7 @@ import os
 import threading
 
 DEFAULT_GRID = {
-    "split_min": [64, 128, 256, 0xFFFFFFFF],
+    "split_min": [64, 48, 128, 0xFFFFFFFF],
     "t_max": [2, 1],
     "blocks": [0],
 }

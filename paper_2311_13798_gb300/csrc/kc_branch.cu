@@ -1884,7 +1884,7 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
             d.t0 = b;
             d.nt = en - b;
             // split the heavy tickets (|VSet| >= split_min) of k >= 7 queries (A12)
-            const u64 smin = cfg->split_min ? cfg->split_min : 128ull;
+            const u64 smin = cfg->split_min ? cfg->split_min : 64ull;
             if (k >= 7 && cfg->split_min != ~0u) {
                 const u64 hb = suffix(std::max<u64>(smin, s_lo));
                 d.nheavy = hb > b ? std::min<u64>(hb - b, d.nt) : 0ull;

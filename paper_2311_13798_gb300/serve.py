@@ -62,7 +62,7 @@ class CudaBackend:
     """libkclique calls on CUDA streams of their own: counts, uploads, and one stream
     per list-worker thread."""
 
-    def __init__(self, device: int = 0, split_min: int = 64):
+    def __init__(self, device: int = 0, split_min: int = 0):
         import torch
 
         from . import kclique as K
@@ -70,8 +70,7 @@ class CudaBackend:
         self.torch = torch
         torch.cuda.set_device(device)
         self.device = device
-        # |VSet| from which the batches split k >= 7 sub-branches (0: the library's default);
-        # on the serving trace 64 balanced the batches better than the default 128
+        # |VSet| from which the batches split k >= 7 sub-branches (0: the library's default, 64)
         self.split_min = int(split_min)
         self.qstream = torch.cuda.Stream()
         self.ustream = torch.cuda.Stream()
