@@ -37,6 +37,9 @@
 #ifndef KC_SCAN_RATIO  // extraction scans a row when its length <= ratio x candidates left
 #define KC_SCAN_RATIO 4
 #endif
+#ifndef KC_MINB8        // resident blocks per SM asked of the compiler, ticket kernel, W = 8
+#define KC_MINB8 4      // (shared memory allows 3; 3 and 4 measured the same on k = 5 and 7)
+#endif
 #ifndef KC_ITEM_MINB8  // resident blocks per SM asked of the compiler, item kernel, W = 8
 #define KC_ITEM_MINB8 6   // (6: 80 registers; 8 % faster than 4 on the power-law k = 7 run)
 #endif
@@ -872,7 +875,7 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
 // resident blocks per SM targeted by the register allocator, per bitset width
 template <int W>
 struct MinBlocks {
-    static constexpr int value = W <= 4 ? 6 : (W <= 8 ? 4 : (W <= 16 ? 2 : 1));
+    static constexpr int value = W <= 4 ? 6 : (W <= 8 ? KC_MINB8 : (W <= 16 ? 2 : 1));
 };
 
 // A heavy sub-branch published for splitting (A12): the coloured, renumbered
