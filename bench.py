@@ -434,6 +434,7 @@ def main(argv=None):
     phase = {"prepare": 0.0, "count": 0.0}
     branch_ms = {k: 0.0 for k in ks}
     word_ops = {k: 0 for k in ks}
+    edge_branches = {k: 0 for k in ks}
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -448,6 +449,7 @@ def main(argv=None):
         for k, r in res.items():
             branch_ms[k] += r["ms_branch"]
             word_ops[k] += r["word_ops"]
+            edge_branches[k] += r["edge_branches"]
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -519,7 +521,11 @@ def main(argv=None):
                            "ms_count": {k: v / args.steps for k, v in branch_ms.items()},
                            "counts": {k: str(r["count"]) for k, r in res.items()}},
                 "clocks": clocks, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
-                "gpu_launches": launches}
+                "gpu_launches": launches,
+                # top-level sub-branches (one per edge with |VSet| >= k-2) run per second of
+                # branch-kernel time, per k
+                "edge_branches_per_s": {k: (edge_branches[k] / (branch_ms[k] / 1e3) if branch_ms[k] else None)
+                                        for k in ks}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
