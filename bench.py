@@ -269,7 +269,7 @@ def run_serve(args):
     import torch
 
     from paper_2311_13798_gb300 import kclique as K
-    from paper_2311_13798_gb300.serve import CudaBackend, KCliqueServer, Request
+    from paper_2311_13798_gb300.serve import KCliqueServer, Request
     from synth import graphs as G
     torch.cuda.set_device(0)
     base = [G.config1(seed=sd) for sd in range(4)] + \
@@ -284,7 +284,7 @@ def run_serve(args):
     cap = 1024
 
     def replay_server():
-        srv = KCliqueServer(CudaBackend(split_min=args.serve_split_min), hbm_budget_bytes=120 << 30)
+        srv = KCliqueServer(hbm_budget_bytes=120 << 30, split_min=args.serve_split_min)
         for j, g in enumerate(base):
             srv.register(f"g{j}", g.row_ptr, g.col, g.n)
         torch.cuda.synchronize()
@@ -296,13 +296,14 @@ def run_serve(args):
                 time.sleep(t - now)
             if kind == "upload":
                 g = uploads[i]
-                req = Request("upload", f"u{i}", csr=(g.row_ptr, g.col, g.n), t_arrival=t0 + t)
+                req = Request("upload", f"u{i}", csr=(g.row_ptr, g.col, g.n))
             else:
-                req = Request(kind, f"g{gid}", k=k, cap=cap, t_arrival=t0 + t)
+                req = Request(kind, f"g{gid}", k=k, cap=cap)
             futs.append(srv.submit(req))
         res = [f.result(timeout=3600) for f in futs]
         srv.close()
-        return srv.stats(), res
+        st = srv.stats()
+        return st, res
 
     def replay_fifo():
         hs = []

@@ -15,8 +15,8 @@
  *   kclique_count /  run, for every edge e whose |VSet(e)| >= k-2, the sub-branch
  *   kclique_list     g_e: greedy colouring, colour-ordered DAG (Sec. 4.3), edge
  *                    branching with pruning Rules (1) and (2), leaves at l = 1 and
- *                    l = 2 (Alg. 2), and early termination on cliques and 2-plexes
- *                    (Sec. 5, Alg. 6).
+ *                    l = 2 (Alg. 2), and early termination on cliques, 2-plexes
+ *                    and 3-plexes (Sec. 5, Alg. 6 and Alg. 7).
  *
  * Conventions
  *   - Vertex ids are uint32 in [0, n).  The input CSR may be non-symmetric and may
@@ -78,8 +78,9 @@ typedef enum {
 typedef struct kc_graph kc_graph; /* opaque, device resident, immutable after prepare */
 
 typedef struct {
-    uint32_t t_max;            /* early termination on t-plexes, t <= t_max (1 or 2); 0 = paper's rule */
-    uint32_t warps_per_block;  /* 0 = library default */
+    uint32_t t_max;            /* early termination on t-plexes, t <= t_max (1, 2 or 3; larger = 3);
+                                  0 = the paper's rule (Sec. 6.1): t = 2 if k <= tau/2, else 3 */
+    uint32_t warps_per_block;  /* warps per persistent block, 1..4 (0 or larger = 4) */
     uint32_t blocks;           /* persistent grid size; 0 = (SMs x resident blocks) */
     uint32_t flags;            /* KC_NO_ET | KC_NO_RULE2 | KC_CHECKSUM | KC_NO_RULE1 */
     uint64_t *d_edge_count;    /* optional device [m]: k-cliques whose first edge is e (mod 2^64) */
@@ -201,6 +202,113 @@ KC_API kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32
  */
 KC_API kc_status kclique_count_batch_noalloc(const kc_graph *const *graphs, const uint32_t *ks, uint32_t nq,
                                              const kc_params *p, kc_stream s, kc_result *results);
+
+/*
+ * ---- Serving: a continuous-batching query server (no counterpart in the paper; the
+ * serving layer around the exact method, whose arithmetic it does not change) ----
+ *
+ * Requests -- count (graph, k), list (graph, k, rows), upload (a host CSR) -- are
+ * submitted at any time and complete asynchronously; kc_server_poll returns their
+ * completions.  Inside, one thread runs every count request waiting when the previous
+ * batch ended as ONE kclique_count_batch call (continuous batching); list_workers
+ * threads write listing rows, each on its own stream (a listing whose buffer filled
+ * gets its exact totals from a count entry that joins the next batch); an upload
+ * thread prepares uploaded graphs on its own stream.  Their work overlaps on the GPU.
+ * Prepared graphs stay resident across requests.  Uploads are admitted against an HBM
+ * budget: the resident bytes of all graphs (kc_info.resident_bytes) plus an estimate
+ * for graphs being prepared may not exceed it; least-recently-used unpinned graphs
+ * that no request waits on are released to make room, and an upload that still does
+ * not fit completes with KC_ERR_OOM.  Each result equals that of the same call made
+ * alone (integer results: exactly).
+ */
+typedef struct kc_server kc_server;
+
+/* The calls the server makes.  NULL in kc_server_config = this library on the GPU
+ * (kclique_prepare / kclique_count_batch with KC_CHECKSUM / kclique_list with
+ * KC_ROWS_ONLY into a device buffer copied to `rows` / kclique_release).  A caller may
+ * pass stand-ins to exercise the scheduling without a GPU.  Graph handles are opaque
+ * to the server.  list: write up to cap rows of k ids to the HOST buffer rows (may be
+ * NULL) and return KC_TRUNCATED with r->written == cap when the buffer filled (totals
+ * then unknown), else KC_OK with the exact totals. */
+typedef struct {
+    void *ctx;
+    kc_status (*prepare)(void *ctx, const uint32_t *row_ptr, const uint32_t *col, uint32_t n, uint64_t nnz,
+                         void **graph, uint64_t *resident_bytes);
+    kc_status (*count_batch)(void *ctx, void *const *graphs, const uint32_t *ks, uint32_t nq, kc_result *results);
+    kc_status (*list)(void *ctx, void *graph, uint32_t k, uint32_t *rows, uint64_t cap, kc_result *r);
+    void (*release)(void *ctx, void *graph);
+} kc_server_backend;
+
+typedef struct {
+    uint64_t hbm_budget_bytes;         /* 0 = 120 GiB */
+    uint32_t max_batch;                /* count requests per batched call; 0 = 512 */
+    uint32_t list_workers;             /* listings in flight at once; 0 = 4 */
+    int32_t device;                    /* CUDA device of the GPU backend; -1 = the current one */
+    uint32_t pad;
+    kc_params params;                  /* for every count batch and listing (per-edge outputs must be NULL) */
+    const kc_server_backend *backend;  /* NULL = the GPU */
+} kc_server_config;
+
+#define KC_REQ_COUNT 0u
+#define KC_REQ_LIST 1u
+#define KC_REQ_UPLOAD 2u
+
+typedef struct {
+    uint32_t kind;            /* KC_REQ_COUNT | KC_REQ_LIST | KC_REQ_UPLOAD */
+    uint32_t k;               /* count / list */
+    uint64_t graph;           /* count / list: a graph id (from kc_server_adopt or an upload) */
+    uint64_t cap;             /* list: rows wanted */
+    uint32_t *rows;           /* list: caller-owned HOST buffer of cap * k uint32 (or NULL), written
+                                 before the completion is posted; keep it alive until then */
+    const uint32_t *row_ptr;  /* upload: host CSR, copied by kc_server_submit */
+    const uint32_t *col;
+    uint32_t n;
+    uint32_t pin;             /* upload: never evicted */
+    uint64_t nnz;
+} kc_request;
+
+typedef struct {
+    uint64_t ticket;          /* as returned by kc_server_submit */
+    uint64_t graph;
+    uint32_t kind, k;
+    int32_t status;           /* kc_status; a listing whose rows were cut at cap: KC_TRUNCATED with exact
+                                 totals; a request on an unknown graph: KC_ERR_INVALID_ARG */
+    uint32_t pad;
+    uint64_t count_lo, count_hi, checksum;
+    uint64_t written;         /* list: rows in rows[] */
+    double t_submit, t_done;  /* seconds on the server's monotonic clock */
+} kc_completion;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, evictions;
+    uint64_t batches, batched_queries, max_batch_seen;
+    uint64_t resident_bytes, graphs, inflight;
+    double busy_count_s, busy_list_s, busy_upload_s;  /* seconds inside backend calls */
+} kc_server_counters;
+
+/* kc_server_create -- start a server (threads, streams).  cfg may be NULL (defaults). */
+KC_API kc_status kc_server_create(const kc_server_config *cfg, kc_server **out);
+
+/* kc_server_adopt -- hand a prepared graph to the server (it releases it when evicted or
+ * destroyed); resident_bytes 0 = take kc_info.resident_bytes (GPU backend).  pin != 0:
+ * never evicted.  *graph_id receives its id. */
+KC_API kc_status kc_server_adopt(kc_server *sv, void *graph, uint64_t resident_bytes, int pin, uint64_t *graph_id);
+
+/* kc_server_submit -- queue a request; *ticket identifies its completion.  graph_id
+ * (may be NULL) receives the graph's id; for an upload it is the new graph's id, and
+ * requests on it may be submitted at once (they wait for its prepare).  Invalid
+ * requests (k < 3, k > KC_MAX_K, null upload arrays) return KC_ERR_INVALID_ARG. */
+KC_API kc_status kc_server_submit(kc_server *sv, const kc_request *req, uint64_t *ticket, uint64_t *graph_id);
+
+/* kc_server_poll -- move up to max completions to out; waits up to wait_ms ms for the
+ * first one (0: no wait, < 0: no limit).  Returns the number moved. */
+KC_API uint32_t kc_server_poll(kc_server *sv, kc_completion *out, uint32_t max, int32_t wait_ms);
+
+KC_API kc_status kc_server_stats(kc_server *sv, kc_server_counters *st);
+
+/* kc_server_destroy -- finish every submitted request, stop the threads, release the
+ * graphs it holds.  Completions not yet polled are dropped. */
+KC_API void kc_server_destroy(kc_server *sv);
 
 /*
  * kclique_int_peak -- measurement utility (no counterpart in the paper): the sustained

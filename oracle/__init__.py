@@ -14,7 +14,8 @@ z(v) = splitmix64(v) | 1, mod 2^64).
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (brute force, complete graphs, Turan graphs, trace(A^3)/6, 2-plex closed forms,
 the Appendix B example, complete bipartite graphs, disjoint unions, relabelings,
-and a second truss-peel algorithm for the levels).
+and a second truss-peel algorithm for the levels); ``sparse_complement_count`` is
+pinned against ``count`` and brute force on 2- and 3-plexes and cocktail-party graphs.
 """
 from __future__ import annotations
 
@@ -194,6 +195,101 @@ def brute_force(g, k: int):
     found = [q for q in itertools.combinations(range(cg.n), k)
              if all(y in adj[x] for x, y in itertools.combinations(q, 2))]
     return len(found), checksum_of(found), found
+
+
+# ------------------------------------------------------------------ sparse complements
+def sparse_complement_count(g, k: int):
+    """Exact k-clique count and checksum of a graph whose complement has maximum degree
+    at most 2 -- a 3-plex in the paper's terms (Sec. 5: every vertex misses at most t = 3
+    vertices counting itself), e.g. K_n minus a matching (a 2-plex) or minus disjoint
+    paths and cycles.  Used where enumeration cannot finish (the 250-vertex 2-plex blocks
+    of the SBM workload at k up to 10).
+
+    The k-cliques of G are the independent k-sets of its complement H.  H is a disjoint
+    union of isolated vertices, paths and cycles; its weighted independence polynomial
+    I(H; x) = sum over independent S of prod_{v in S} (z_v x) is the product of those of
+    its components, and the k-clique count and checksum are the x^k coefficients of
+    I(H; x) with z = 1 and with z = the keys.  A path's polynomial follows from the
+    recurrence I(P_{v1..vm}) = I(P_{v2..vm}) + z_{v1} x I(P_{v3..vm}) (v1 out / v1 in);
+    a cycle's is I(P_{v2..vm}) + z_{v1} x I(P_{v3..v(m-1)}).  Exact Python integers;
+    the checksum is reduced mod 2^64 at the end.  Raises ValueError if the complement
+    has a vertex of degree > 2.
+    """
+    cg = _clean(g)
+    n = cg.n
+    deg = np.diff(cg.row_ptr.astype(np.int64))
+    active = np.nonzero(deg > 0)[0]
+    # vertices without edges belong to no clique of size >= 2; the graph is taken on the
+    # vertices that have edges (ids kept), as a subgraph of the SBM is
+    vs = active.tolist()
+    idx = {v: i for i, v in enumerate(vs)}
+    nv = len(vs)
+    nbr = [set() for _ in range(nv)]
+    for a, b in zip(cg.eu.tolist(), cg.ev.tolist()):
+        nbr[idx[a]].add(idx[b])
+        nbr[idx[b]].add(idx[a])
+    miss = []
+    for i in range(nv):
+        m = [j for j in range(nv) if j != i and j not in nbr[i]]
+        if len(m) > 2:
+            raise ValueError("the complement has a vertex of degree > 2")
+        miss.append(m)
+    z = [key(v) for v in vs]
+
+    def mul(a, b):
+        out = [0] * (k + 1)
+        for i, x in enumerate(a):
+            if x:
+                for j, y in enumerate(b[: k + 1 - i]):
+                    out[i + j] += x * y
+        return out
+
+    def path_poly(seq, w):
+        # I(P) over the vertex sequence seq, truncated at x^k
+        if not seq:
+            return [1] + [0] * k
+        prev2 = [1] + [0] * k                      # I of the empty suffix
+        prev1 = [1] + [0] * k
+        prev1[1] = w[seq[-1]]                      # I of the last vertex alone
+        if k < 1:
+            prev1 = prev1[:1]
+        for v in reversed(seq[:-1]):
+            cur = [prev1[j] + (w[v] * prev2[j - 1] if j >= 1 else 0) for j in range(k + 1)]
+            prev2, prev1 = prev1, cur
+        return prev1
+
+    def component_polys(w):
+        seen = [False] * nv
+        total = [1] + [0] * k
+        for start in range(nv):
+            if seen[start] or len(miss[start]) == 2:
+                continue
+            seq, prev, cur = [], -1, start          # a path from an end (or an isolated vertex)
+            while cur != -1:
+                seen[cur] = True
+                seq.append(cur)
+                nxt = [x for x in miss[cur] if x != prev]
+                prev, cur = cur, (nxt[0] if nxt else -1)
+            total = mul(total, path_poly(seq, w))
+        for start in range(nv):
+            if seen[start]:
+                continue
+            seq, prev, cur = [], -1, start          # a cycle
+            while not seen[cur]:
+                seen[cur] = True
+                seq.append(cur)
+                nxt = [x for x in miss[cur] if x != prev]
+                prev, cur = cur, nxt[0]
+            v1 = seq[0]
+            out_v1 = path_poly(seq[1:], w)
+            in_v1 = path_poly(seq[2:-1], w)
+            poly = [out_v1[j] + (w[v1] * in_v1[j - 1] if j >= 1 else 0) for j in range(k + 1)]
+            total = mul(total, poly)
+        return total
+
+    cnt = component_polys([1] * nv)[k]
+    cs = component_polys(z)[k] & MASK64
+    return {"count": cnt, "checksum": cs}
 
 
 # ------------------------------------------------------------------ edges

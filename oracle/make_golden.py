@@ -10,6 +10,14 @@ so a long run can be stopped and resumed.
     python oracle/make_golden.py c2 5 7 9      # minutes to hours
     python oracle/make_golden.py c2edges 9     # per-edge sub-branch values at k = 9
     python oracle/make_golden.py c3blocks 6 7  # per-block values for the SBM workload
+    python oracle/make_golden.py c3plex        # closed forms of its 2-plex blocks, k = 6..10
+    python oracle/make_golden.py c3cross       # its cliques with an inter-block edge, k = 6..10
+    python oracle/make_golden.py c3dense 6     # every dense block at k (resumable; hours)
+
+The SBM workload (50,000 vertices, 200 blocks of 250) is pinned as a decomposition:
+every k-clique either lies inside one block or holds an inter-block edge, so
+    count(G) = sum over blocks of count(block) + count(cliques with an inter-block edge),
+and the same for the checksum (mod 2^64), block graphs keeping the original ids.
 """
 import json
 import os
@@ -113,6 +121,49 @@ def main(argv):
             cg = O.CleanGraph.of(sub)
             for k in ks or [6, 7]:
                 _count_entry(f"c3/block{b}", cg, k, threads)
+    elif what in ("c3plex", "c3cross", "c3dense"):
+        g, info = G.sbm_2plex()
+        _store("c3/graph", {"fingerprint": g.fingerprint(), "n": g.n, "m": g.m,
+                            "two_plex_blocks": info["two_plex_blocks"]})
+        blk = info["block_of"]
+        u, v = g.edges()
+        if what == "c3plex":
+            # each 2-plex block: K_250 minus a matching, closed form (pinned against
+            # enumeration in tests/test_oracle_pins.py)
+            out = {}
+            t = time.time()
+            for b in info["two_plex_blocks"]:
+                keep = (blk[u] == b) & (blk[v] == b)
+                sub = G.from_edges(g.n, u[keep], v[keep])
+                out[str(b)] = {str(k): [str(r["count"]), str(r["checksum"])]
+                               for k in (ks or range(6, 11))
+                               for r in [O.sparse_complement_count(sub, k)]}
+            _store("c3/plex_blocks", {"blocks": out, "wall_s": round(time.time() - t, 2)})
+        elif what == "c3cross":
+            # cliques with at least one inter-block edge: put every inter-block edge first
+            # in the edge order (round 0, the rest round 1); the sub-branches of Eq. 2 then
+            # list each such clique exactly once, at its first inter-block edge
+            cg = O.CleanGraph.of(g)
+            cross = blk[cg.eu] != blk[cg.ev]
+            rounds = np.where(cross, 0, 1).astype(np.uint32)
+            edges = np.nonzero(cross)[0]
+            for k in ks or range(6, 11):
+                t = time.time()
+                cnt, cs = O.edge_counts(cg, k, rounds, edges, threads=threads)
+                _store(f"c3/cross_k{k}", {"count": str(sum(cnt)), "checksum": str(sum(cs) & ((1 << 64) - 1)),
+                                          "cross_edges": int(edges.size), "wall_s": round(time.time() - t, 2),
+                                          "threads": threads})
+        else:
+            dense = [b for b in range(200) if b not in set(info["two_plex_blocks"])]
+            have = _load()
+            for k in ks or [6]:
+                for b in dense:
+                    key = f"c3/dense{b}/k{k}"
+                    if key in have:
+                        continue
+                    keep = (blk[u] == b) & (blk[v] == b)
+                    sub = G.from_edges(g.n, u[keep], v[keep])
+                    _count_entry(f"c3/dense{b}", O.CleanGraph.of(sub), k, threads)
     else:
         raise SystemExit(__doc__)
 

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libkclique.so")
-SOURCES = ["kc_prepare.cu", "kc_branch.cu", "kc_api.cu", "kc_noalloc.cu"]
+SOURCES = ["kc_prepare.cu", "kc_branch.cu", "kc_api.cu", "kc_noalloc.cu", "kc_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]

@@ -47,13 +47,9 @@ struct DeviceGuard {
     }
 };
 
-// Early-termination threshold t (Sec. 6.1 "Baselines and Metrics": t = 2 when
-// k <= tau/2, else 3).  The kernels implement the closed forms for t <= 2, so a
-// request for t >= 3 runs with t = 2.
-u32 pick_t(const kc_params *p) {
-    u32 t = (p && p->t_max) ? p->t_max : 2u;
-    return std::min<u32>(t, 2u);
-}
+// Early-termination threshold: the caller's t_max, or 0 for the paper's rule, which
+// the launch code resolves per query from k and tau (kc_pick_t)
+u32 pick_t(const kc_params *p) { return p ? p->t_max : 0u; }
 
 kc_status map_device_status(unsigned st) {
     if (st & KC_DEV_ERR_OVERFLOW) return KC_ERR_OVERFLOW;

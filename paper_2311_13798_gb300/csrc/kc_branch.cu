@@ -77,7 +77,7 @@ struct QDesc {
     const u32 *row_ptr, *col, *pos_eid, *pos_round, *eu, *ev, *round, *vset, *tickets;
     const u64 *vset_ptr;
     u32 k;
-    u32 pad;
+    u32 t_max;        // early termination on t-plexes, t <= t_max (0: none)
     u64 t0;           // first ticket (index into tickets) of this launch's range
     u64 nt;           // tickets in range
     u64 nheavy;       // the first nheavy tickets of the range are split (k >= 7)
@@ -600,10 +600,193 @@ __device__ void write_clique(u32 *out, u64 slot, u32 k, const u32 *ids, int nids
 
 
 // ---------------------------------------------------------------- A9 early termination
+// kCtPlex for t = 3 (Sec. 5.2, Alg. 7) in closed form.  In a 3-plex every vertex of C
+// misses at most two others, so the inverse graph H (the missing pairs) has maximum
+// degree 2: a disjoint union of isolated vertices (the universal ones), paths and
+// cycles.  The l-cliques of g[C] are the independent l-sets of H, so their number is
+// the x^l coefficient of H's independence polynomial, the product over its components;
+// with a weight z_v per vertex the same coefficient is the checksum sum over those
+// cliques of prod z_v.  Alg. 7 reaches the same sets by branching on the inverse graph
+// (the I-set combinations times the branches on the non-universal vertices); the
+// product form counts them without enumerating.
+//
+// The warp evaluates the polynomial lane per coefficient (lane j holds x^j; l <= 30)
+// with one dynamic-programming step per vertex, walking H component by component:
+// a = sets of the vertices seen so far whose last vertex is not taken, b = last taken;
+// a vertex v of weight z: a' = a + b, b' = z * x * (a, or a + b when v starts a new
+// component).  A cycle v1..vm runs two tracks (v1 out / v1 in) and drops the sets
+// that take both v1 and vm.  Counts use z = 1 in saturating 128-bit arithmetic,
+// the checksum uses the keys mod 2^64.
+struct Poly2 {
+    u128 ca, cb;  // counts
+    u64 sa, sb;   // key-weighted sums
+};
+
+__device__ __forceinline__ u128 shfl_up_u128(u128 v, int lane) {
+    const u64 lo = __shfl_up_sync(0xffffffffu, (u64)v, 1);
+    const u64 hi = __shfl_up_sync(0xffffffffu, (u64)(v >> 64), 1);
+    return lane == 0 ? (u128)0 : (((u128)hi << 64) | (u128)lo);
+}
+
+// one vertex of weight z; fresh: v starts a new component (no edge to the previous vertex)
+template <bool SUM>
+__device__ __forceinline__ void poly_step(Poly2 &p, u64 z, bool fresh, int lane) {
+    const u128 tot = add_sat(p.ca, p.cb);
+    const u128 sh = shfl_up_u128(fresh ? tot : p.ca, lane);
+    p.ca = tot;
+    p.cb = sh;
+    if (SUM) {
+        const u64 st = p.sa + p.sb;
+        const u64 ss = __shfl_up_sync(0xffffffffu, fresh ? st : p.sa, 1);
+        p.sa = st;
+        p.sb = lane == 0 ? 0ull : ss * z;
+    }
+}
+
+// returns false if the walk met an inconsistent partner table (bounded; reported)
+template <int W, bool SUM>
+__device__ bool plex3_poly(const Lay &L, const u32 (&cw)[W], int cnt, int l, int lane, uint16_t *pr, u128 *cnt_l,
+                           u64 *sum_l) {
+    constexpr int RS = W + KC_ROW_PAD;
+    u32 *D1 = L.tmpW, *NU = L.tmpW2;  // D1: one missing partner; NU: at least one
+    if (lane < W) { D1[lane] = 0; NU[lane] = 0; }
+    __syncwarp();
+    // partners of every vertex of C (at most two), by position
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        if (i < cnt) {
+            const int x = L.aux2[i];
+            int p1 = 0xFFFF, p2 = 0xFFFF;
+            if (L.aux[i] < cnt - 1) {
+#pragma unroll
+                for (int w = 0; w < W; w++) {
+                    u32 nb = cw[w] & ~L.A[x * RS + w] & ~((w == (x >> 5)) ? (1u << (x & 31)) : 0u);
+                    while (nb) {
+                        const int y = w * 32 + __ffs(nb) - 1;
+                        nb &= nb - 1;
+                        if (p1 == 0xFFFF) p1 = y; else if (p2 == 0xFFFF) p2 = y;
+                    }
+                }
+                if (KC_OK(x >> 5, W)) {
+                    atomicOr(&NU[x >> 5], 1u << (x & 31));
+                    if (p2 == 0xFFFF) atomicOr(&D1[x >> 5], 1u << (x & 31));
+                }
+            }
+            if (KC_OK(x, 32 * W)) { pr[2 * x] = (uint16_t)p1; pr[2 * x + 1] = (uint16_t)p2; }
+        }
+    }
+    __syncwarp();
+    u32 uni = 0, d1 = 0;  // this lane's word of the universal and the path-end vertices
+    if (lane < W) { uni = cw[lane] & ~NU[lane]; d1 = D1[lane]; }
+    __syncwarp();
+    u32 *Vis = L.tmpW2;  // visited non-universal vertices
+    if (lane < W) Vis[lane] = uni;
+    __syncwarp();
+    Poly2 p;
+    p.ca = lane == 0 ? (u128)1 : (u128)0;
+    p.cb = 0;
+    p.sa = lane == 0 ? 1ull : 0ull;
+    p.sb = 0;
+    int steps = 0;
+    // isolated vertices of H (universal in g[C]), one component each
+    while (true) {
+        const unsigned bal = __ballot_sync(0xffffffffu, uni != 0);
+        if (!bal) break;
+        const int fl = __ffs(bal) - 1;
+        const u32 wv = __shfl_sync(0xffffffffu, uni, fl);
+        const int v = fl * 32 + __ffs(wv) - 1;
+        if (lane == fl) uni &= uni - 1;
+        poly_step<SUM>(p, SUM ? L.z[v] : 0ull, true, lane);
+        if (++steps > cnt) return false;
+    }
+    // paths, each walked from an end vertex; then the cycles (what is left)
+    for (int pass = 0; pass < 2; pass++) {
+        while (true) {
+            u32 cand = 0;
+            if (lane < W) cand = cw[lane] & ~Vis[lane] & (pass == 0 ? d1 : 0xFFFFFFFFu);
+            const unsigned bal = __ballot_sync(0xffffffffu, cand != 0);
+            if (!bal) break;
+            const int fl = __ffs(bal) - 1;
+            const u32 wv = __shfl_sync(0xffffffffu, cand, fl);
+            int v = fl * 32 + __ffs(wv) - 1;
+            if (pass == 0) {  // a path from its end v
+                int prev = -1;
+                bool fresh = true;
+                while (v >= 0) {
+                    if (!KC_OK(v, 32 * W)) return false;
+                    __syncwarp();
+                    if (lane == 0) Vis[v >> 5] |= 1u << (v & 31);
+                    poly_step<SUM>(p, SUM ? L.z[v] : 0ull, fresh, lane);
+                    fresh = false;
+                    if (++steps > cnt) return false;
+                    const int q1 = pr[2 * v], q2 = pr[2 * v + 1];
+                    int nx = (q1 != prev) ? q1 : q2;
+                    if (nx == 0xFFFF) nx = -1;
+                    prev = v;
+                    v = nx;
+                }
+                __syncwarp();
+                continue;
+            }
+            // a cycle v1 = v, v2, ..., vm (every vertex has two partners)
+            const u64 z1 = SUM ? L.z[v] : 0ull;
+            Poly2 t1;  // the track with v1 taken
+            {
+                const u128 tot = add_sat(p.ca, p.cb);
+                t1.ca = 0;
+                t1.cb = shfl_up_u128(tot, lane);
+                p.ca = tot;
+                p.cb = 0;
+                t1.sa = 0;
+                t1.sb = 0;
+                if (SUM) {
+                    const u64 st = p.sa + p.sb;
+                    const u64 ss = __shfl_up_sync(0xffffffffu, st, 1);
+                    t1.sb = lane == 0 ? 0ull : ss * z1;
+                    p.sa = st;
+                    p.sb = 0;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) Vis[v >> 5] |= 1u << (v & 31);
+            if (++steps > cnt) return false;
+            const int v1 = v;
+            int prev = v1, cur = pr[2 * v1];
+            while (cur != v1) {
+                if (cur == 0xFFFF || !KC_OK(cur, 32 * W)) return false;
+                __syncwarp();
+                if (lane == 0) Vis[cur >> 5] |= 1u << (cur & 31);
+                const u64 zc = SUM ? L.z[cur] : 0ull;
+                poly_step<SUM>(p, zc, false, lane);
+                poly_step<SUM>(t1, zc, false, lane);
+                if (++steps > cnt) return false;
+                const int q1 = pr[2 * cur], q2 = pr[2 * cur + 1];
+                const int nx = (q1 != prev) ? q1 : q2;
+                prev = cur;
+                cur = nx;
+            }
+            __syncwarp();
+            // drop the sets holding both v1 and vm (t1.cb); fold into a fresh state
+            p.ca = add_sat(add_sat(p.ca, p.cb), t1.ca);
+            p.cb = 0;
+            if (SUM) {
+                p.sa = p.sa + p.sb + t1.sa;
+                p.sb = 0;
+            }
+        }
+    }
+    const u128 c = add_sat(p.ca, p.cb);
+    const u64 lo = __shfl_sync(0xffffffffu, (u64)c, l), hi = __shfl_sync(0xffffffffu, (u64)(c >> 64), l);
+    *cnt_l = ((u128)hi << 64) | (u128)lo;
+    *sum_l = SUM ? __shfl_sync(0xffffffffu, p.sa + p.sb, l) : 0ull;
+    return steps == cnt;
+}
+
 // Returns true if the frame is closed (pruned by size or counted in closed form).
+// pr: scratch of 2 x 32W u16 (a free child slot of the next depth) for the t = 3 form
 template <int W, int MODE>
 __device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l, u64 P, int lane, Acc &acc,
-                                bool et_allowed, int ws) {
+                                bool et_allowed, int ws, uint16_t *pr, int tmax) {
     u32 cw[W];
     int cnt = 0;
 #pragma unroll
@@ -613,7 +796,6 @@ __device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l
     }
     if (cnt < l) return true;
     if (!et_allowed) return false;
-    const int tmax = (int)a.t_max;
     // degrees inside C, lane per vertex (early exit as soon as some vertex is too sparse)
     int mind = cnt;
     for (int base = 0; base < cnt; base += 32) {
@@ -633,10 +815,22 @@ __device__ bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l
         if (mind < cnt - tmax) return false;
     }
     __syncwarp();
-    const int t = cnt - mind;  // 1: clique, 2: 2-plex
+    const int t = cnt - mind;  // 1: clique, 2: 2-plex, 3: 3-plex
     u128 add = 0;
     u64 csum = 0;
     const bool want_sum = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
+    if (t >= 3) {
+        u64 s3 = 0;
+        if (!plex3_poly<W, (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0>(L, cw, cnt, l, lane, pr, &add, &s3)) {
+            acc.status |= KC_DEV_ERR_BOUNDS;
+            return true;
+        }
+        if (add == SAT128) acc.status |= KC_DEV_ERR_OVERFLOW;
+        acc.cf = add_sat(acc.cf, add);
+        acc.cf_csum += want_sum ? s3 * P : 0ull;
+        if (lane == 0) acc.et++;
+        return true;
+    }
     if (t <= 1) {
         add = binom(a.binom, cnt, l);
     } else {
@@ -977,7 +1171,8 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
     constexpr bool LIST = (MODE & MODE_LIST) != 0;
     const bool use_rule1 = !(a.flags & KC_NO_RULE1);
     const bool use_rule2 = !(a.flags & KC_NO_RULE2);
-    const bool use_et = !(a.flags & KC_NO_ET) && a.t_max >= 1;
+    const int tq = (int)q.t_max;
+    const bool use_et = !(a.flags & KC_NO_ET) && tq >= 1;
     const u32 k = q.k;
     long long tsec = 0;
     if (lane < W) L.C0[lane] = lt_mask(s, lane);
@@ -999,7 +1194,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
             if (l == 3 && (!LIST || full)) {
                 const long long tf = (KC_SECTION_PROFILE && prof) ? clock64() : 0;
                 KC_SEC_BEGIN();
-                frame_l3_count<W, SUM>(L, C, lane, acc, (int)a.t_max, use_et, Ws, P);
+                frame_l3_count<W, SUM>(L, C, lane, acc, min(tq, 2), use_et, Ws, P);
                 KC_SEC_END(3);
                 if (KC_SECTION_PROFILE && prof && a.l3hist) {
                     const int c = warp_popc<W>(C, lane);
@@ -1013,7 +1208,8 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                 continue;
             }
             KC_SEC_BEGIN();
-            const bool closed = early_terminate<W, MODE>(L, a, C, l, P, lane, acc, use_et && (!LIST || full), Ws);
+            const bool closed = early_terminate<W, MODE>(L, a, C, l, P, lane, acc, use_et && (!LIST || full), Ws,
+                                                         (uint16_t *)(L.childC + (size_t)((d + 1) * 32) * W), tq);
             KC_SEC_END(2);
             if (closed) { phase = 3; continue; }
             if (lane == 0) { L.cur[d] = d == 0 ? u_lo - 1 : -1; L.rn[d] = 0; }
@@ -1066,7 +1262,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                         u32 *Bm = L.Bm + slot * W, *M1 = L.M1 + slot * W;
                         if (lane < W) { Bm[lane] = 0; M1[lane] = 0; }
                         __syncwarp();
-                        const int tm = (int)a.t_max;
+                        const int tm = min(tq, 2);
                         for (int base = 0; base < ncu; base += 32) {
                             const int i = base + lane;
                             if (i < ncu) {
@@ -1275,7 +1471,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                     // l = 3 child: the t-plex test and the Alg. 6 count in this lane (a lane
                     // leaves the test at its first vertex of too small degree); SUM: the x^3
                     // coefficient of prod (1 + c x), c = z_f (universal) or z_a + z_b (pair)
-                    const int tmax = (int)a.t_max;
+                    const int tmax = min(tq, 2);  // the in-lane forms cover t <= 2
                     const int w0 = cv >> 5;  // the child's set has no bits below v's word
                     int nuni = 0;
                     bool plex = true;
@@ -1381,7 +1577,6 @@ branch_kernel(Args a) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const Lay L = make_lay<W>(smem + (size_t)wib * a.warp_bytes, a.D, SUM);
-    const bool use_et = !(a.flags & KC_NO_ET) && a.t_max >= 1;
     const bool use_rule1 = !(a.flags & KC_NO_RULE1);
     const bool prof = KC_SECTION_PROFILE && a.prof != 0;
     long long tsec = 0;
@@ -1406,6 +1601,7 @@ branch_kernel(Args a) {
         const QDesc &q = a.qs[qi];
         const u32 k = q.k;
         const int l0 = (int)k - 2;
+        const bool use_et = !(a.flags & KC_NO_ET) && q.t_max >= 1;
         const u64 tq = t - a.qstart[qi];
         const u32 e = q.tickets[q.t0 + tq];
         const long long t_start = clock64();
@@ -1490,7 +1686,7 @@ branch_kernel(Args a) {
                 __syncwarp();
                 if (lane == 0) acc.nodes++;
                 KC_SEC_BEGIN();
-                frame_l3_count<W, SUM>(L, L.C0, lane, acc, (int)a.t_max, use_et, Ws, P0);
+                frame_l3_count<W, SUM>(L, L.C0, lane, acc, min((int)q.t_max, 2), use_et, Ws, P0);
                 KC_SEC_END(3);
             } else {
                 KC_SEC_BEGIN();
@@ -1512,7 +1708,9 @@ branch_kernel(Args a) {
                     __syncwarp();
                     if (lane == 0) acc.nodes++;
                     KC_SEC_BEGIN();
-                    const bool closed = early_terminate<W, MODE>(L, a, L.C0, l0, P0, lane, acc, use_et, Ws);
+                    const bool closed = early_terminate<W, MODE>(L, a, L.C0, l0, P0, lane, acc, use_et, Ws,
+                                                                 (uint16_t *)(L.childC + (size_t)32 * W),
+                                                                 (int)q.t_max);
                     KC_SEC_END(2);
                     const int limu = min(s, use_rule1 ? (int)L.lim[min(l0, 32 * W + 1)] : s);
                     if (closed || limu <= 0) {
@@ -1679,7 +1877,9 @@ std::mutex g_tables_mu;
 template <typename K>
 kc_status geometry(K kern, u32 warp_bytes, u64 work, const kc_run_cfg *cfg, u64 *blocks, int *wpb_out, size_t *smem_out,
                    u32 block_bytes = 0) {
-    int wpb = WARPS_PER_BLOCK_DEFAULT;
+    // warps per block: the caller's choice within the kernels' launch bound, else the default
+    int wpb = (cfg->warps_per_block >= 1 && cfg->warps_per_block <= (u32)WARPS_PER_BLOCK_DEFAULT)
+                  ? (int)cfg->warps_per_block : WARPS_PER_BLOCK_DEFAULT;
     int dev = 0, max_optin = 0, nsm = 0;
     KC_CUDA(cudaGetDevice(&dev));
     KC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -1792,6 +1992,14 @@ kc_status launch_mode(int W, const Args &a, const std::vector<QDesc> &qs, const 
 }  // namespace
 #ifndef KC_EMU
 
+// early-termination threshold of one query: the caller's t_max (at most 3: the kernels
+// hold closed forms for cliques, 2-plexes and 3-plexes), or the paper's rule (Sec. 6.1
+// "Baselines and Metrics": t = 2 when k <= tau / 2, else t = 3)
+u32 kc_pick_t(u32 t_max, u32 k, u32 tau) {
+    if (t_max) return std::min<u32>(t_max, 3u);
+    return 2ull * k <= (u64)tau ? 2u : 3u;
+}
+
 kc_status kc_ensure_tables(cudaStream_t s) {
     int dev = 0;
     KC_CUDA(cudaGetDevice(&dev));
@@ -1884,6 +2092,7 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
             d.eu = g->eu; d.ev = g->ev; d.round = g->round; d.vset = g->vset; d.tickets = g->tickets;
             d.vset_ptr = g->vset_ptr;
             d.k = k;
+            d.t_max = kc_pick_t(cfg->t_max, k, g->tau);
             d.t0 = b;
             d.nt = en - b;
             // split the heavy tickets (|VSet| >= split_min) of k >= 7 queries (A12)
@@ -2039,8 +2248,8 @@ constexpr u32 kNoallocMaxQ = 64;
 u64 align256(u64 x) { return (x + 255ull) & ~255ull; }
 
 template <int W, int MODE>
-kc_status launch_class_fixed(const Args &a0, const QDesc *qs, u32 nqs, cudaStream_t s, QDesc *d_qs, u64 *d_qstart,
-                             unsigned long long *d_ctr) {
+kc_status launch_class_fixed(const Args &a0, const QDesc *qs, u32 nqs, const kc_run_cfg *cfg, cudaStream_t s,
+                             QDesc *d_qs, u64 *d_qstart, unsigned long long *d_ctr) {
     Args a = a0;
     u32 D = 1;
     for (u32 i = 0; i < nqs; i++) {
@@ -2061,12 +2270,10 @@ kc_status launch_class_fixed(const Args &a0, const QDesc *qs, u32 nqs, cudaStrea
     a.nq = nqs;
     a.ticket_ctr = d_ctr;
     a.slots = nullptr;
-    kc_run_cfg cfg;
-    memset(&cfg, 0, sizeof(cfg));
     u64 blocks = 1;
     int wpb = 1;
     size_t smem = 0;
-    kc_status st = geometry(branch_kernel<W, MODE>, a.warp_bytes, qstart[nqs], &cfg, &blocks, &wpb, &smem);
+    kc_status st = geometry(branch_kernel<W, MODE>, a.warp_bytes, qstart[nqs], cfg, &blocks, &wpb, &smem);
     if (st != KC_OK) return st;
     branch_kernel<W, MODE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
     kc_note_launch();
@@ -2075,19 +2282,40 @@ kc_status launch_class_fixed(const Args &a0, const QDesc *qs, u32 nqs, cudaStrea
 }
 
 template <int MODE>
-kc_status launch_fixed(int W, const Args &a, const QDesc *qs, u32 nqs, cudaStream_t s, QDesc *d_qs, u64 *d_qstart,
-                       unsigned long long *d_ctr) {
+kc_status launch_fixed(int W, const Args &a, const QDesc *qs, u32 nqs, const kc_run_cfg *cfg, cudaStream_t s,
+                       QDesc *d_qs, u64 *d_qstart, unsigned long long *d_ctr) {
     switch (W) {
-        case 1: return launch_class_fixed<1, MODE>(a, qs, nqs, s, d_qs, d_qstart, d_ctr);
-        case 2: return launch_class_fixed<2, MODE>(a, qs, nqs, s, d_qs, d_qstart, d_ctr);
-        case 4: return launch_class_fixed<4, MODE>(a, qs, nqs, s, d_qs, d_qstart, d_ctr);
-        case 8: return launch_class_fixed<8, MODE>(a, qs, nqs, s, d_qs, d_qstart, d_ctr);
-        case 16: return launch_class_fixed<16, MODE>(a, qs, nqs, s, d_qs, d_qstart, d_ctr);
-        case 32: return launch_class_fixed<32, MODE>(a, qs, nqs, s, d_qs, d_qstart, d_ctr);
+        case 1: return launch_class_fixed<1, MODE>(a, qs, nqs, cfg, s, d_qs, d_qstart, d_ctr);
+        case 2: return launch_class_fixed<2, MODE>(a, qs, nqs, cfg, s, d_qs, d_qstart, d_ctr);
+        case 4: return launch_class_fixed<4, MODE>(a, qs, nqs, cfg, s, d_qs, d_qstart, d_ctr);
+        case 8: return launch_class_fixed<8, MODE>(a, qs, nqs, cfg, s, d_qs, d_qstart, d_ctr);
+        case 16: return launch_class_fixed<16, MODE>(a, qs, nqs, cfg, s, d_qs, d_qstart, d_ctr);
+        case 32: return launch_class_fixed<32, MODE>(a, qs, nqs, cfg, s, d_qs, d_qstart, d_ctr);
     }
     return KC_ERR_UNSUPPORTED;
 }
+
+// load the code of one kernel instance now (module loading is lazy by default: the
+// first launch of an instance would otherwise load it, which takes device memory)
+template <typename K>
+kc_status preload(K kern) {
+    cudaFuncAttributes fa;
+    KC_CUDA(cudaFuncGetAttributes(&fa, kern));
+    return KC_OK;
+}
 }  // namespace
+
+// Every kernel instance the no-allocation path can launch, loaded at its set-up.
+kc_status kc_preload_fixed_kernels() {
+    kc_status st = KC_OK;
+#define KC_PRELOAD_W(W)                                                      \
+    if (st == KC_OK) st = preload(branch_kernel<W, 0>);                     \
+    if (st == KC_OK) st = preload(branch_kernel<W, MODE_CHECKSUM>);
+    KC_PRELOAD_W(1) KC_PRELOAD_W(2) KC_PRELOAD_W(4) KC_PRELOAD_W(8) KC_PRELOAD_W(16) KC_PRELOAD_W(32)
+#undef KC_PRELOAD_W
+    if (st == KC_OK) st = preload(binom_kernel);
+    return st;
+}
 
 kc_status kc_fill_binom(u128 *table, cudaStream_t s) {
     binom_kernel<<<1, 64, 0, s>>>(table);
@@ -2102,9 +2330,10 @@ u64 kc_scratch_bytes_for(u32 nq) {
            align256(sizeof(u64) * ((u64)nq + 1)) + align256(4 * sizeof(unsigned long long));
 }
 
-kc_status kc_run_queries_in_scratch(const kc_query *qv, u32 nq, u32 t_max, u32 flags, cudaStream_t s,
+kc_status kc_run_queries_in_scratch(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cudaStream_t s,
                                     unsigned char *d_scratch, u64 scratch_bytes, const u128 *d_binom,
                                     kc_dev_acc *h_acc) {
+    const u32 t_max = cfg->t_max, flags = cfg->flags;
     if (nq == 0) return KC_OK;
     if (nq > kNoallocMaxQ || kc_scratch_bytes_for(nq) > scratch_bytes) return KC_ERR_INVALID_ARG;
     unsigned char *p = d_scratch;
@@ -2146,13 +2375,14 @@ kc_status kc_run_queries_in_scratch(const kc_query *qv, u32 nq, u32 t_max, u32 f
             d.eu = g->eu; d.ev = g->ev; d.round = g->round; d.vset = g->vset; d.tickets = g->tickets;
             d.vset_ptr = g->vset_ptr;
             d.k = k;
+            d.t_max = kc_pick_t(t_max, k, g->tau);
             d.t0 = b;
             d.nt = en - b;
             d.acc = d_acc + i;
         }
         if (!nqs) continue;
-        st = mode == 0 ? launch_fixed<0>(W, a, qs, nqs, s, d_qs, d_qstart, d_ctr)
-                       : launch_fixed<MODE_CHECKSUM>(W, a, qs, nqs, s, d_qs, d_qstart, d_ctr);
+        st = mode == 0 ? launch_fixed<0>(W, a, qs, nqs, cfg, s, d_qs, d_qstart, d_ctr)
+                       : launch_fixed<MODE_CHECKSUM>(W, a, qs, nqs, cfg, s, d_qs, d_qstart, d_ctr);
         // the query table in scratch is rewritten for the next class
         if (st == KC_OK) KC_CUDA(cudaStreamSynchronize(s));
     }

@@ -76,7 +76,7 @@ struct kc_query {
 };
 
 struct kc_run_cfg {
-    u32 t_max;
+    u32 t_max;          // 0: the paper's rule per query (kc_pick_t); else at most 3
     u32 flags;
     u32 warps_per_block;
     u32 blocks;
@@ -109,6 +109,9 @@ struct kc_dev_acc {
 kc_status kc_run_queries(const kc_query *q, u32 nq, const kc_run_cfg *cfg, cudaStream_t s,
                          kc_dev_acc *h_acc, float *ms, float *ms_branch);
 
+// early-termination threshold t of one query (0 = the paper's rule)
+u32 kc_pick_t(u32 t_max, u32 k, u32 tau);
+
 // binomial table on the device (saturating u128), built on first use per device
 kc_status kc_ensure_tables(cudaStream_t s);
 
@@ -118,9 +121,10 @@ kc_status kc_ensure_tables(cudaStream_t s);
 // ---- no-allocation count path (kc_noalloc.cu): scratch and table supplied by the caller
 kc_status kc_fill_binom(u128 *table, cudaStream_t s);
 u64 kc_scratch_bytes_for(u32 nq);
-kc_status kc_run_queries_in_scratch(const kc_query *q, u32 nq, u32 t_max, u32 flags, cudaStream_t s,
+kc_status kc_run_queries_in_scratch(const kc_query *q, u32 nq, const kc_run_cfg *cfg, cudaStream_t s,
                                     unsigned char *d_scratch, u64 scratch_bytes, const u128 *d_binom,
                                     kc_dev_acc *h_acc);
+kc_status kc_preload_fixed_kernels();
 void kc_set_last_error_msg(const char *msg);
 
 // ---- small host helpers

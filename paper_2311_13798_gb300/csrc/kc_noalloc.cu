@@ -16,9 +16,16 @@
 //     the graph), so very heavy k >= 7 queries run slower than through kclique_count;
 //   * per-edge outputs of kc_params are not supported (rejected as KC_ERR_INVALID_ARG);
 //   * the first call on a device does a one-time set-up with that device current: it
-//     looks up the device addresses of the static arrays (cudaGetSymbolAddress) and
-//     fills the static binomial table with one kernel.  Make that first call before
-//     any stream capture;
+//     looks up the device addresses of the static arrays (cudaGetSymbolAddress), loads
+//     the code of every kernel this path can launch (module loading is lazy by default,
+//     and loading a kernel takes device memory) and fills the static binomial table
+//     with one kernel.  Make that first call early -- before any stream capture, and
+//     before the process is at its device-memory limit;
+//   * the set-up is kept per device index for the life of the process: after a
+//     cudaDeviceReset (or any teardown of the device's primary context) the cached
+//     addresses are stale, so the entry point must not be used across a reset;
+//   * kc_params.warps_per_block and .blocks act as for kclique_count_batch; the
+//     timings ms_count and ms_branch are left at 0 (timing would need events);
 //   * every call on a device shares the same scratch array, which keeps the previous
 //     call's contents (the accumulators are cleared at the start of each call).  Calls
 //     that overlap on the GPU -- from different host threads or streams -- race on it;
@@ -60,7 +67,9 @@ kc_status noalloc_setup(int dev, cudaStream_t s, NoallocDevice **out) {
         void *sc = nullptr, *bt = nullptr;
         KC_CUDA(cudaGetSymbolAddress(&sc, kc_noalloc_scratch));
         KC_CUDA(cudaGetSymbolAddress(&bt, kc_noalloc_binom));
-        kc_status st = kc_fill_binom((u128 *)bt, s);
+        kc_status st = kc_preload_fixed_kernels();
+        if (st != KC_OK) return st;
+        st = kc_fill_binom((u128 *)bt, s);
         if (st != KC_OK) return st;
         d.scratch = (unsigned char *)sc;
         d.binom = (u128 *)bt;
@@ -118,11 +127,15 @@ extern "C" KC_API kc_status kclique_count_batch_noalloc(const kc_graph *const *g
     if (prev != dev) KC_CUDA(cudaSetDevice(dev));
     NoallocDevice *nd = nullptr;
     kc_status st = noalloc_setup(dev, s, &nd);
-    const u32 t = (p && p->t_max) ? (p->t_max < 2u ? p->t_max : 2u) : 2u;
+    kc_run_cfg cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.t_max = p ? p->t_max : 0u;  // 0: the paper's rule per query
+    cfg.flags = p ? p->flags : 0u;
+    cfg.warps_per_block = p ? p->warps_per_block : 0u;
+    cfg.blocks = p ? p->blocks : 0u;
     kc_dev_acc acc[KC_NOALLOC_MAX_QUERIES];
     if (st == KC_OK)
-        st = kc_run_queries_in_scratch(qv, nrun, t, p ? p->flags : 0u, s, nd->scratch, KC_NOALLOC_SCRATCH_BYTES,
-                                       nd->binom, acc);
+        st = kc_run_queries_in_scratch(qv, nrun, &cfg, s, nd->scratch, KC_NOALLOC_SCRATCH_BYTES, nd->binom, acc);
     if (prev != dev) cudaSetDevice(prev);
     if (st != KC_OK) return st;
     kc_status worst = KC_OK;

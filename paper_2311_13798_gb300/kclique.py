@@ -54,6 +54,51 @@ class KcInfo(C.Structure):
                 ("max_degree", C.c_uint32), ("rounds", C.c_uint64), ("resident_bytes", C.c_uint64)]
 
 
+# ---- serving (kc_server_*)
+KC_REQ_COUNT = 0
+KC_REQ_LIST = 1
+KC_REQ_UPLOAD = 2
+
+_PREPARE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32, C.c_uint64,
+                          C.POINTER(C.c_void_p), C.POINTER(C.c_uint64))
+_COUNT_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32), C.c_uint32,
+                        C.POINTER(KcResult))
+_LIST_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.c_uint64,
+                       C.POINTER(KcResult))
+_RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class KcServerBackend(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("prepare", _PREPARE_FN), ("count_batch", _COUNT_FN), ("list", _LIST_FN),
+                ("release", _RELEASE_FN)]
+
+
+class KcServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_batch", C.c_uint32), ("list_workers", C.c_uint32),
+                ("device", C.c_int32), ("pad", C.c_uint32), ("params", KcParams),
+                ("backend", C.POINTER(KcServerBackend))]
+
+
+class KcRequest(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("k", C.c_uint32), ("graph", C.c_uint64), ("cap", C.c_uint64),
+                ("rows", C.c_void_p), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("n", C.c_uint32),
+                ("pin", C.c_uint32), ("nnz", C.c_uint64)]
+
+
+class KcCompletion(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("graph", C.c_uint64), ("kind", C.c_uint32), ("k", C.c_uint32),
+                ("status", C.c_int32), ("pad", C.c_uint32), ("count_lo", C.c_uint64), ("count_hi", C.c_uint64),
+                ("checksum", C.c_uint64), ("written", C.c_uint64), ("t_submit", C.c_double),
+                ("t_done", C.c_double)]
+
+
+class KcServerCounters(C.Structure):
+    _fields_ = [(f, C.c_uint64) for f in ("submitted", "completed", "rejected", "evictions", "batches",
+                                          "batched_queries", "max_batch_seen", "resident_bytes", "graphs",
+                                          "inflight")] + \
+               [(f, C.c_double) for f in ("busy_count_s", "busy_list_s", "busy_upload_s")]
+
+
 class KCliqueError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -104,6 +149,18 @@ def _load():
             lib.kclique_count_batch_noalloc.restype = C.c_int
             lib.kclique_count_batch_noalloc.argtypes = [C.POINTER(vp), C.POINTER(u32), u32, C.POINTER(KcParams), vp,
                                                         C.POINTER(KcResult)]
+            lib.kc_server_create.restype = C.c_int
+            lib.kc_server_create.argtypes = [C.POINTER(KcServerConfig), C.POINTER(vp)]
+            lib.kc_server_adopt.restype = C.c_int
+            lib.kc_server_adopt.argtypes = [vp, vp, u64, C.c_int, C.POINTER(u64)]
+            lib.kc_server_submit.restype = C.c_int
+            lib.kc_server_submit.argtypes = [vp, C.POINTER(KcRequest), C.POINTER(u64), C.POINTER(u64)]
+            lib.kc_server_poll.restype = u32
+            lib.kc_server_poll.argtypes = [vp, C.POINTER(KcCompletion), u32, C.c_int32]
+            lib.kc_server_stats.restype = C.c_int
+            lib.kc_server_stats.argtypes = [vp, C.POINTER(KcServerCounters)]
+            lib.kc_server_destroy.restype = None
+            lib.kc_server_destroy.argtypes = [vp]
             lib.kclique_count_batch.restype = C.c_int
             lib.kclique_count_batch.argtypes = [C.POINTER(vp), C.POINTER(u32), u32, C.POINTER(KcParams), vp,
                                                 C.POINTER(KcResult)]

@@ -49,11 +49,13 @@ GRAPHS = {
     "chung_lu": lambda: G.chung_lu(n=4000, w_max=400.0, i0=40.0, planted=6, planted_min=12, planted_max=30, seed=5),
     "sbm": lambda: G.sbm_2plex(blocks=8, block_size=60, p_in=0.85, p_out=0.01, two_plex_blocks=3, seed=6)[0],
     "wide": lambda: G.gnp(300, 0.75, seed=7),   # sub-branches of ~170 vertices (6 words)
+    "t3plex_big": lambda: G.t_plex(90, 3, seed=11),   # inverse graph: paths and cycles
+    "t4plex": lambda: G.t_plex(64, 4, seed=12),
 }
 
 
 # largest k the oracle finishes in seconds on each graph
-KMAX = {"wide": 5, "gnp400": 6}
+KMAX = {"wide": 5, "gnp400": 6, "t3plex_big": 6, "t4plex": 7}
 
 
 @pytest.fixture(scope="module")
@@ -112,22 +114,39 @@ def test_ablation_flags_do_not_change_results(cache, name, flags):
         assert K.kclique_count(h, k, flags=flags)["count"] == want["count"], (name, k, flags)
 
 
-@pytest.mark.parametrize("t_max", [1, 2])
+@pytest.mark.parametrize("t_max", [1, 2, 3, 0])
 def test_early_termination_thresholds(cache, t_max):
-    for name in ("k70", "two_plex", "t3plex", "sbm"):
+    """t_max 1..3 and 0 (the paper's rule: t = 2 if k <= tau/2, else 3) give the oracle's
+    results; t = 3 closes 3-plex frames through the inverse graph's paths and cycles."""
+    for name in ("k70", "two_plex", "t3plex", "t3plex_big", "t4plex", "sbm", "gnp120_dense"):
         g, cg, h = get(cache, name)
-        for k in (5, 6, 8):
+        for k in (4, 5, 6, 7):
+            if k > KMAX.get(name, 9):
+                continue
             want = O.count(cg, k)
             got = kc().kclique_count(h, k, t_max=t_max, flags=kc().KC_CHECKSUM)
-            assert (got["count"], got["checksum"]) == (want["count"], want["checksum"])
-            assert kc().kclique_count(h, k, t_max=t_max)["count"] == want["count"]
+            assert (got["count"], got["checksum"]) == (want["count"], want["checksum"]), (name, k, t_max)
+            assert kc().kclique_count(h, k, t_max=t_max)["count"] == want["count"], (name, k, t_max)
+            for split_min in (3, 0xFFFFFFFF):
+                r = kc().kclique_count(h, k, t_max=t_max, split_min=split_min, flags=kc().KC_CHECKSUM)
+                assert (r["count"], r["checksum"]) == (want["count"], want["checksum"]), (name, k, t_max)
 
 
-def test_early_termination_fires_on_cliques_and_2plexes(cache):
+def test_early_termination_fires_on_cliques_and_plexes(cache):
     for name in ("k70", "two_plex"):
         g, cg, h = get(cache, name)
         got = kc().kclique_count(h, 6)
         assert got["et_hits"] > 0
+    # a 3-plex: every sub-branch is a 3-plex, closed at its top frame with t = 3 only
+    # (at k = 5 the top frame already has l = 3, which the l = 3 routine counts exactly
+    # whatever t is, so the difference shows from k = 6 on)
+    g, cg, h = get(cache, "t3plex_big")
+    for k in (5, 6):
+        t2 = kc().kclique_count(h, k, t_max=2)
+        t3 = kc().kclique_count(h, k, t_max=3)
+        assert t3["count"] == t2["count"] == O.count(cg, k)["count"]
+        if k >= 6:
+            assert t3["et_hits"] > 0 and t3["nodes"] < t2["nodes"]
 
 
 @pytest.mark.parametrize("name", ["gnp60", "gnp120_dense", "k40", "turan", "two_plex", "t3plex", "appendix_b",

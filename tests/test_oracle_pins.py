@@ -291,3 +291,68 @@ def test_sample_of_tops_is_additive():
     b = O.count(g, 4, tops=np.arange(100, 200))
     assert a["count"] + b["count"] == full["count"]
     assert (a["checksum"] + b["checksum"]) & M64 == full["checksum"]
+
+
+def _complement_of(n, missing):
+    """K_n minus the given pairs."""
+    miss = {(min(a, b), max(a, b)) for a, b in missing}
+    a, b = np.triu_indices(n, 1)
+    keep = np.array([(int(x), int(y)) not in miss for x, y in zip(a, b)], dtype=bool)
+    return G.from_edges(n, a[keep], b[keep])
+
+
+@pytest.mark.parametrize("maker,ks", [
+    (lambda: G.two_plex(5, 4), (3, 4, 5, 6)),
+    (lambda: G.two_plex(0, 6), (3, 6, 7)),
+    (lambda: G.t_plex(30, 3, seed=2), (3, 4, 5, 6)),
+    (lambda: G.t_plex(14, 3, seed=7), (3, 4, 5, 6, 7)),
+    (lambda: G.complete_multipartite([3] * 8), (3, 4, 5, 8, 9)),           # complement: triangles
+    (lambda: _complement_of(12, [(i, (i + 1) % 12) for i in range(12)]), (3, 4, 5, 6, 7)),  # C_12
+    (lambda: _complement_of(11, [(i, i + 1) for i in range(10)]), (3, 4, 5, 6)),           # P_11
+    (lambda: _complement_of(13, [(0, 1), (1, 2), (2, 0), (3, 4), (4, 5), (5, 6), (6, 3), (7, 8)]), (3, 5, 7)),
+    (lambda: G.complete(9), (3, 5, 9)),
+])
+def test_sparse_complement_closed_form(maker, ks):
+    """Cliques of G = independent sets of its complement; for a complement of paths and
+    cycles the product of their independence polynomials matches enumeration."""
+    g = maker()
+    for k in ks:
+        a = O.sparse_complement_count(g, k)
+        b = O.count(g, k, shortcut=False)
+        assert (a["count"], a["checksum"]) == (b["count"], b["checksum"]), k
+        if g.n <= 14:
+            bf_c, bf_s, _ = O.brute_force(g, k)
+            assert (a["count"], a["checksum"]) == (bf_c, bf_s)
+
+
+def test_sparse_complement_rejects_denser_complement():
+    g = _complement_of(8, [(0, 1), (0, 2), (0, 3)])
+    with pytest.raises(ValueError):
+        O.sparse_complement_count(g, 3)
+
+
+def test_block_decomposition_of_sbm():
+    """Every clique lies in one block or holds an inter-block edge: with the inter-block
+    edges first in the edge order, their sub-branches (Eq. 2) hold exactly the latter,
+    and the blocks plus that term give the whole."""
+    g, info = G.sbm_2plex(blocks=6, block_size=40, p_in=0.8, p_out=0.08, two_plex_blocks=2, seed=3)
+    blk = info["block_of"]
+    cg = O.CleanGraph.of(g)
+    cross = blk[cg.eu] != blk[cg.ev]
+    rounds = np.where(cross, 0, 1).astype(np.uint32)
+    u, v = g.edges()
+    for k in (3, 4, 5):
+        cnt, cs = O.edge_counts(cg, k, rounds, np.nonzero(cross)[0])
+        parts = [O.count(G.from_edges(g.n, u[(blk[u] == b) & (blk[v] == b)], v[(blk[u] == b) & (blk[v] == b)]), k)
+                 for b in range(6)]
+        whole = O.count(g, k)
+        assert sum(cnt) > 0 or k > 3
+        assert whole["count"] == sum(p["count"] for p in parts) + sum(cnt)
+        assert whole["checksum"] == (sum(p["checksum"] for p in parts) + sum(cs)) & M64
+    for b in info["two_plex_blocks"]:
+        keep = (blk[u] == b) & (blk[v] == b)
+        sub = G.from_edges(g.n, u[keep], v[keep])
+        for k in (4, 6):
+            a = O.sparse_complement_count(sub, k)
+            r = O.count(sub, k)
+            assert (a["count"], a["checksum"]) == (r["count"], r["checksum"])
