@@ -13,9 +13,11 @@ value = k-cliques counted per second (sum over the three counts / step time).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle (the only reference: the paper ships no code) on
-a bounded sample of the same workload on this machine's host cores.
-Multi-GPU (torchrun): every rank runs the same step on its own graph (seed = rank),
-no data-path collective; value = all ranks' cliques / max rank time ("weak").
+a bounded, deterministic sample of the same workload on this machine's host cores.
+Multi-GPU (torchrun): every rank prepares the same graph and counts its share of the
+top-level sub-branches (ticket ranges cut between |VSet| sizes, balanced by estimated
+cost); one all-reduce of the exact counts ends the step; value = the graph's cliques /
+max rank time ("strong": the total work is fixed).
 """
 from __future__ import annotations
 
@@ -31,9 +33,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# k = 9 on this graph holds ~1e16-1e17 cliques; the paper's ET (t <= 2) leaves billions of
-# small frames and one pass takes tens of minutes, so the default step runs k = 5 and 7
-# (see the design doc for the k = 9 shard measurements); --ks 5,7,9 runs all three.
+# k = 9 on this graph holds ~1.4e17 cliques and one full pass takes minutes, so the timed
+# step runs k = 5 and 7 and the line adds a k = 9 record of the heaviest sub-branches;
+# --ks 5,7,9 puts all three in the timed step.
 KS = (5, 7)
 WORKLOAD = "chung_lu n=1e6 m=1.0e7 exp=2.1 wmax=1e4 +200 cliques(30-60)"
 LIST_K = 5
@@ -50,7 +52,9 @@ def parse(argv=None):
     ap.add_argument("--ks", default=",".join(map(str, KS)))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-k9", action="store_true", help="skip the k = 9 record after the timed steps")
+    ap.add_argument("--k9-tickets", type=int, default=2000,
+                    help="k = 9 record: the heaviest this many sub-branches (tickets [0, n))")
     ap.add_argument("--workload", choices=["power_law", "batch", "serve", "probe"], default="power_law",
                     help="power_law: the default bench line; batch / serve: the batching and serving "
                          "measurements (separate JSON lines); probe: one count on a Chung-Lu graph sized "
@@ -150,25 +154,35 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- reference arm
-def cpu_oracle_rate(g, k: int, seconds: float, seed: int = 0) -> dict:
-    """The CPU oracle (as it stands) on a bounded random sample of top vertices of g."""
+# one vertex in SAMPLE_STRIDE[k] of the vertices sorted by degree (descending, ties by id):
+# a systematic sample, so every degree stratum is represented (its counts scaled by the
+# stride estimate the whole graph's within a few per cent)
+SAMPLE_STRIDE = {5: 8, 7: 128, 9: 4096}
+
+
+def cpu_oracle_rate(g, ks) -> dict:
+    """The CPU oracle, as it stands, on the same deterministic sample of top vertices in
+    both the bench leg and the reference arm: cliques counted per second of its run."""
     import numpy as np
 
     import oracle as O
     cg = O.CleanGraph.of(g)
     threads = O.threads_default()
-    rng = np.random.default_rng(seed)
-    order = rng.permutation(g.n).astype(np.uint32)
-    done, cnt, spent, chunk = 0, 0, 0.0, 2048
-    while spent < seconds and done < g.n:
-        tops = order[done: done + chunk]
+    deg = np.diff(cg.row_ptr.astype(np.int64))
+    order = np.lexsort((np.arange(g.n), -deg)).astype(np.uint32)
+    cnt, spent, parts = 0, 0.0, []
+    for k in ks:
+        stride = SAMPLE_STRIDE.get(k, 4096)
+        tops = np.ascontiguousarray(order[::stride])
         t0 = time.perf_counter()
         r = O.count(cg, k, shortcut=True, checksum=False, threads=threads, tops=tops)
-        spent += time.perf_counter() - t0
+        el = time.perf_counter() - t0
         cnt += r["count"]
-        done += tops.size
-        chunk = min(chunk * 2, 1 << 18)
-    return {"cliques": cnt, "seconds": spent, "tops": done, "threads": threads}
+        spent += el
+        parts.append(f"k={k}: every {stride}th vertex by degree ({tops.size} top vertices), {el:.1f} s")
+    return {"rate": cnt / spent if spent else 0.0, "cliques": cnt, "seconds": spent, "threads": threads,
+            "sample": "the oracle's degeneracy-ordered vertex branching with the clique shortcut, count only, "
+                      "rooted at a systematic sample of the vertices sorted by degree: " + "; ".join(parts)}
 
 
 def run_reference(args):
@@ -178,25 +192,19 @@ def run_reference(args):
     from synth import graphs as G
     g = G.chung_lu(seed=0)
     ks = [int(x) for x in args.ks.split(",")]
-    per = max(1.0, args.cpu_seconds / len(ks))
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm state worth warming; kept for the contract
-    tot_c, tot_s, tops, thr = 0, 0.0, 0, 1
-    for step in range(args.steps):
-        for k in ks:
-            r = cpu_oracle_rate(g, k, per / max(args.steps, 1), seed=step * 100 + k)
-            tot_c += r["cliques"]
-            tot_s += r["seconds"]
-            tops += r["tops"]
-            thr = r["threads"]
+    # the oracle has no warm state; every step runs the same bounded sample
+    tot_c, tot_s, r = 0, 0.0, None
+    for _ in range(args.steps):
+        r = cpu_oracle_rate(g, ks)
+        tot_c += r["cliques"]
+        tot_s += r["seconds"]
     val = tot_c / tot_s if tot_s else 0.0
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "k-cliques/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / max(args.steps, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD + f", k={','.join(map(str, ks))}", "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": val, "unit": "k-cliques/s", "cores": thr, "kind": "oracle",
-                             "sample": f"{tops} random top vertices of the degeneracy-ordered vertex branching, "
-                                       f"k in {ks}, {tot_s:.1f} s"},
+            "cpu_baseline": {"value": val, "unit": "k-cliques/s", "cores": r["threads"], "kind": "oracle",
+                             "sample": r["sample"]},
             "e2e": {"value": val, "unit": "k-cliques/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -382,6 +390,11 @@ def run_probe(args):
                           "et_hits": r["et_hits"], "kernel_rev": K.kclique_kernel_rev()}), flush=True)
 
 
+def golden():
+    path = os.path.join(ROOT, "tests", "golden", "configs.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
@@ -401,6 +414,7 @@ def main(argv=None):
     import torch.distributed as dist
 
     from paper_2311_13798_gb300 import kclique as K
+    from paper_2311_13798_gb300 import shard
     from synth import graphs as G
 
     rank, world, local = dist_env()
@@ -408,19 +422,33 @@ def main(argv=None):
     if world > 1:
         dist.init_process_group("nccl")
     ks = [int(x) for x in args.ks.split(",")]
-    g = G.chung_lu(seed=rank)
+    # every rank holds the same graph; the ranks split its top-level sub-branches
+    g = G.chung_lu(seed=0)
     rp = torch.from_numpy(g.row_ptr.astype(np.int32)).cuda()
     col = torch.from_numpy(g.col.astype(np.int32)).cuda()
     out = torch.empty((LIST_CAP, LIST_K), dtype=torch.int32, device="cuda")
+    out_h = torch.empty((LIST_CAP, LIST_K), dtype=torch.int32).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     stream = torch.cuda.current_stream()
+    h0 = K.kclique_prepare(rp, col, g.n)
+    vs = K.kclique_edge_data(h0)["vset_size"]
+    # this rank's ticket range per k: cut between |VSet| sizes, balanced by estimated cost
+    shards = {k: shard.partition_by_size(vs, k, world)[rank] for k in set(ks) | {LIST_K, 9}}
+    h0.release()
 
     def step(host=False, rp_h=None, col_h=None):
         h = K.kclique_prepare(rp_h, col_h, g.n) if host else K.kclique_prepare(rp, col, g.n)
-        res = {k: K.kclique_count(h, k) for k in ks}
-        lst = K.kclique_list(h, LIST_K, out)
+        res = {k: K.kclique_count(h, k, ticket_begin=shards[k][0], ticket_end=shards[k][1]) for k in ks}
+        lst = K.kclique_list(h, LIST_K, out, ticket_begin=shards[LIST_K][0], ticket_end=shards[LIST_K][1])
+        if host:  # the listing's rows and the results go back to the host
+            out_h[: lst["written"]].copy_(out[: lst["written"]], non_blocking=True)
         h.release()
         return res, lst
+
+    def reduce_counts(res):
+        if world == 1:
+            return {k: r["count"] for k, r in res.items()}
+        return {k: shard.allreduce_result(r["count"], 0)[0] for k, r in res.items()}
 
     for _ in range(args.warmup):
         res, lst = step()
@@ -432,20 +460,22 @@ def main(argv=None):
     sampler.start()
     torch.cuda.synchronize()
     times, cliques = [], 0
-    phase = {"prepare": 0.0, "count": 0.0}
+    phase = {"prepare": 0.0}
     branch_ms = {k: 0.0 for k in ks}
     word_ops = {k: 0 for k in ks}
     edge_branches = {k: 0 for k in ks}
+    totals = {}
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         res, lst = step()
+        totals = reduce_counts(res)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-        cliques += sum(r["count"] for r in res.values())
+        cliques += sum(totals.values())
         phase["prepare"] += lst["ms_prepare"]
         for k, r in res.items():
             branch_ms[k] += r["ms_branch"]
@@ -461,11 +491,9 @@ def main(argv=None):
         t = torch.tensor([my_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot_ms = float(t.item())
-        allc = allgather_ints([cliques], world)
-        total_cliques = combine_counts([c[0] for c in allc])
     else:
-        tot_ms, total_cliques = my_ms, cliques
-    value = total_cliques / (tot_ms / 1e3)
+        tot_ms = my_ms
+    value = cliques / (tot_ms / 1e3)
 
     e2e = None
     if not args.no_e2e:
@@ -473,58 +501,86 @@ def main(argv=None):
         col_h = torch.from_numpy(g.col.astype(np.int32)).pin_memory()
         step(True, rp_h, col_h)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
-        n_e2e, c_e2e = max(1, min(args.steps, 2)), 0
+        n_e2e, c_e2e, rows = max(1, min(args.steps, 2)), 0, 0
         for _ in range(n_e2e):
-            res, lst = step(True, rp_h, col_h)
-            c_e2e += sum(r["count"] for r in res.values())
+            res_e, lst_e = step(True, rp_h, col_h)
+            c_e2e += sum(reduce_counts(res_e).values())
+            rows = lst_e["written"]
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
         e2e = {"value": c_e2e / el, "unit": "k-cliques/s",
                "h2d_bytes_per_step": int(4 * (g.n + 1) + 4 * g.col.size),
-               "d2h_bytes_per_step": int(72 * (len(ks) + 1))}
+               # the listing's rows plus one result record per call
+               "d2h_bytes_per_step": int(4 * LIST_K * rows + 72 * (len(ks) + 1))}
 
-    # roofline of the dominant kernel (the branch kernels of kclique_count): algorithmic
+    # self-check against the oracle's stored values (outside the timed region): the
+    # counts of the timed steps, and the checksums from one pass with KC_CHECKSUM
+    gold = golden()
+    verified = None
+    if all(f"c2/k{k}" in gold for k in ks) and g.fingerprint() == gold.get("c2/graph", {}).get("fingerprint"):
+        h = K.kclique_prepare(rp, col, g.n)
+        sums = {}
+        for k in ks:
+            r = K.kclique_count(h, k, flags=K.KC_CHECKSUM, ticket_begin=shards[k][0], ticket_end=shards[k][1])
+            c, cs = (r["count"], r["checksum"]) if world == 1 else shard.allreduce_result(r["count"], r["checksum"])
+            sums[k] = (c, cs)
+        h.release()
+        verified = all(str(totals[k]) == gold[f"c2/k{k}"]["count"] and str(sums[k][0]) == gold[f"c2/k{k}"]["count"]
+                       and str(sums[k][1]) == gold[f"c2/k{k}"]["checksum"] for k in ks)
+
+    # k = 9 on the same graph: its heaviest sub-branches (a fixed ticket range) timed once
+    # after the steps; the full pass takes minutes and is recorded with the profiles
+    k9 = None
+    if not args.no_k9 and 9 not in ks:
+        h = K.kclique_prepare(rp, col, g.n)
+        tb, te = 0, min(args.k9_tickets, shards[9][1])
+        r = K.kclique_count(h, 9, ticket_begin=tb, ticket_end=te) if rank == 0 and te > tb else None
+        h.release()
+        if r is not None:
+            k9 = {"tickets": [tb, te], "count": str(r["count"]), "ms_branch": r["ms_branch"],
+                  "k-cliques/s": r["count"] / (r["ms_branch"] / 1e3) if r["ms_branch"] else None,
+                  "edge_branches_per_s": r["edge_branches"] / (r["ms_branch"] / 1e3) if r["ms_branch"] else None}
+
+    # roofline of the dominant kernels (the branch kernels of kclique_count): algorithmic
     # bitset lane-ops (3 per word of every candidate-set intersection, 2 per word of every
     # degree test, counted in-kernel) over their CUDA-event time, against the measured
     # AND+AND+POPC peak of this GPU
     peak = K.kclique_int_peak()["lane_ops_per_s"]
     ops_all, ms_all = sum(word_ops.values()), sum(branch_ms.values())
     achieved = ops_all / (ms_all / 1e3) if ms_all else 0.0
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        tj = json.load(open(tpath))
-        if tj.get("kernel_rev") == K.kclique_kernel_rev():
-            traffic = tj.get("bytes_per_launch")
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "G lane-ops/s",
-            "frac": achieved / peak if peak else None, "traffic": traffic,
+            "frac": achieved / peak if peak else None, "traffic": None,
             "kernel": "branch_kernel + branch_items_kernel (all width classes), measured live with CUDA events",
             "peak_kind": "measured AND+AND+POPC microbenchmark (kclique_int_peak) on this GPU"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        tot_c, tot_s, tops, thr = 0, 0.0, 0, 1
-        for k in ks:
-            r = cpu_oracle_rate(g, k, args.cpu_seconds / len(ks), seed=k)
-            tot_c += r["cliques"]; tot_s += r["seconds"]; tops += r["tops"]; thr = r["threads"]
-        cpu = {"value": tot_c / tot_s if tot_s else 0.0, "unit": "k-cliques/s", "cores": thr, "kind": "oracle",
-               "sample": f"{tops} random top vertices of the oracle's degeneracy-ordered vertex branching "
-                         f"on the same graph, k in {ks}, {tot_s:.1f} s of CPU time"}
+        r = cpu_oracle_rate(g, ks)
+        cpu = {"value": r["rate"], "unit": "k-cliques/s", "cores": r["threads"], "kind": "oracle",
+               "sample": r["sample"]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "k-cliques/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": WORKLOAD + f", k={','.join(map(str, ks))} + list k={LIST_K} cap 2^24",
                            "graph": g.fingerprint(), "m": g.m,
+                           "parallelism": f"{world} rank(s), one graph split by |VSet| ranges",
                            "l2": "flushed (256 MB write) before every step",
                            "ms_prepare": phase["prepare"] / args.steps,
                            "ms_count": {k: v / args.steps for k, v in branch_ms.items()},
-                           "counts": {k: str(r["count"]) for k, r in res.items()}},
+                           "counts": {k: str(v) for k, v in totals.items()},
+                           "verified": verified, "k9": k9},
                 "clocks": clocks, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
                 "gpu_launches": launches,
                 # top-level sub-branches (one per edge with |VSet| >= k-2) run per second of
-                # branch-kernel time, per k
+                # branch-kernel time, per k (this rank's)
                 "edge_branches_per_s": {k: (edge_branches[k] / (branch_ms[k] / 1e3) if branch_ms[k] else None)
                                         for k in ks}}
         print(json.dumps(line), flush=True)

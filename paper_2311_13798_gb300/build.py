@@ -17,7 +17,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libkclique.so")
-SOURCES = ["kc_prepare.cu", "kc_branch.cu", "kc_api.cu", "kc_noalloc.cu", "kc_server.cu"]
+WIDTHS = (1, 2, 4, 8, 16, 32)
+SOURCES = (["kc_prepare.cu", "kc_branch.cu"] + [f"kc_branch_w{w}.cu" for w in WIDTHS] +
+           ["kc_api.cu", "kc_noalloc.cu", "kc_server.cu"])
+HEADERS = ["kc_internal.cuh", "kc_branch_dev.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
@@ -41,7 +44,7 @@ def kernel_rev() -> str:
     """Short hash of the CUDA sources (identifies the kernels behind stored ncu counters)."""
     import hashlib
     h = hashlib.sha256()
-    for src in SOURCES + ["kc_internal.cuh"]:
+    for src in SOURCES + HEADERS:
         h.update(open(os.path.join(CSRC, src), "rb").read())
     return h.hexdigest()[:12]
 
@@ -49,7 +52,7 @@ def kernel_rev() -> str:
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(OUT, exist_ok=True)
     extra = list(extra or []) + [f'-DKC_KERNEL_REV="{kernel_rev()}"']
-    headers = [os.path.join(CSRC, "kc_internal.cuh"), os.path.join(HERE, "..", "include", "kclique.h")]
+    headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", "kclique.h")]
     objs = []
     jobs = []
     for src in SOURCES:
@@ -66,7 +69,9 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         if r.returncode:
             raise RuntimeError(f"nvcc failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
         return r.stderr
-    with cf.ThreadPoolExecutor(max_workers=len(jobs) or 1) as ex:
+    # the widest translation units take longest: start them first
+    jobs.sort(key=lambda c: -max((w for w in WIDTHS if f"kc_branch_w{w}.cu" in c[-3]), default=0))
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 1) or 1) as ex:
         for err in ex.map(run, jobs):
             if verbose and err:
                 print(err, file=sys.stderr)

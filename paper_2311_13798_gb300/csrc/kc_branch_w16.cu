@@ -1,0 +1,6 @@
+// The branch kernels and their launches for bitset width W = 16 (sub-branches of
+// 257..512 vertices); see kc_branch_dev.cuh.
+#define KC_BRANCH_INSTANTIATE
+#include "kc_branch_dev.cuh"
+
+KC_BRANCH_WIDTH(16)

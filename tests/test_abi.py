@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "kclique.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(kclique_\w+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b((?:kclique|kc_server)_\w+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():
@@ -36,8 +36,8 @@ def test_library_exports_every_declared_symbol():
 def test_binding_names_match_the_abi():
     from paper_2311_13798_gb300 import kclique
     for name in _declared():
-        if name in ("kclique_release", "kclique_last_error"):
-            continue
+        if name in ("kclique_release", "kclique_last_error") or name.startswith("kc_server_"):
+            continue  # the server's calls are wrapped by serve.KCliqueServer
         assert hasattr(kclique, name), name
 
 
@@ -49,6 +49,24 @@ def test_binding_rejects_bad_arguments_without_gpu():
     assert lib.kclique_count(None, 4, None, None, ctypes.byref(r)) == kclique.KC_ERR_INVALID_ARG
     h = ctypes.c_void_p()
     assert lib.kclique_prepare(None, None, 0, 0, 0, None, ctypes.byref(h)) == kclique.KC_ERR_INVALID_ARG
+
+
+def test_server_structs_match_the_header():
+    """The binding's server structs have the sizes of the C ones (fields of 8-byte
+    alignment in the order the header gives)."""
+    from paper_2311_13798_gb300 import kclique as K
+    assert ctypes.sizeof(K.KcRequest) == 4 + 4 + 8 + 8 + 8 + 8 + 8 + 4 + 4 + 8
+    assert ctypes.sizeof(K.KcCompletion) == 8 + 8 + 4 + 4 + 4 + 4 + 8 * 4 + 8 + 8
+    assert ctypes.sizeof(K.KcServerBackend) == 5 * 8
+    assert ctypes.sizeof(K.KcServerConfig) == 8 + 4 + 4 + 4 + 4 + ctypes.sizeof(K.KcParams) + 8
+
+
+def test_server_rejects_bad_requests_without_gpu():
+    from paper_2311_13798_gb300 import kclique as K
+    lib = K.library()
+    t = ctypes.c_uint64()
+    assert lib.kc_server_submit(None, None, ctypes.byref(t), None) == K.KC_ERR_INVALID_ARG
+    assert lib.kc_server_create(None, None) == K.KC_ERR_INVALID_ARG
 
 
 def test_flag_and_limit_constants_match_the_header():

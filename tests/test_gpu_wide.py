@@ -98,7 +98,8 @@ def test_two_plex_600(cache):
                 poly[j] += poly[j - 1] * c
         got = K().kclique_count(h, k, flags=K().KC_CHECKSUM)
         assert (got["count"], got["checksum"]) == (cnt, poly[k] & M64), k
-        assert got["et_hits"] > 0
+        if k >= 5:  # k = 4 counts the edges of each sub-branch: no frame to close
+            assert got["et_hits"] > 0
 
 
 def test_cocktail_party_600_with_t3(cache):
