@@ -211,12 +211,16 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm
 def run_batch(args):
-    """Many small uneven graphs, each with its own k: one kclique_count_batch call
-    (one persistent launch per width class) against one kclique_count per graph."""
+    """Many small uneven graphs, each with its own k (config 4's shape): one batched call
+    with the library defaults, one with the autotuner's per-query picks, against one
+    kclique_count per graph; every result checked equal across the three."""
+    import collections
+
     import numpy as np
     import torch
 
     from paper_2311_13798_gb300 import kclique as K
+    from paper_2311_13798_gb300.autotune import Autotuner
     from synth import graphs as G
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
@@ -233,28 +237,39 @@ def run_batch(args):
     torch.cuda.synchronize()
     prep_s = time.perf_counter() - t0
     ks = [sp["k"] for sp in specs]
-    for _ in range(args.warmup):
-        K.kclique_count_batch(handles, ks)
-    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        res_b = K.kclique_count_batch(handles, ks)
-    torch.cuda.synchronize()
-    batch_s = (time.perf_counter() - t0) / args.steps
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        res_s = [K.kclique_count(h, k) for h, k in zip(handles, ks)]
-    torch.cuda.synchronize()
-    single_s = (time.perf_counter() - t0) / args.steps
-    assert [r["count"] for r in res_b] == [r["count"] for r in res_s]
+    tuner = Autotuner(shard=256, reps=1)
+    choices = [tuner.choice(h, k) for h, k in zip(handles, ks)]
+    tune_s = time.perf_counter() - t0
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            r = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) / args.steps, r
+
+    batch_s, res_b = timed(lambda: K.kclique_count_batch(handles, ks, flags=K.KC_CHECKSUM))
+    tuned_s, res_t = timed(lambda: K.kclique_count_batch(handles, ks, choices=choices, flags=K.KC_CHECKSUM))
+    single_s, res_s = timed(lambda: [K.kclique_count(h, k, flags=K.KC_CHECKSUM) for h, k in zip(handles, ks)])
+    key = [(r["count"], r["checksum"]) for r in res_s]
+    same = [(r["count"], r["checksum"]) for r in res_b] == key == [(r["count"], r["checksum"]) for r in res_t]
     cliques = sum(r["count"] for r in res_b)
-    line = {"metric": "batched k-clique queries/s", "workload": "batch", "value": len(ks) / batch_s,
-            "unit": "queries/s", "one_query_per_launch": len(ks) / single_s, "speedup": single_s / batch_s,
-            "k-cliques/s": cliques / batch_s, "n_graphs": len(ks), "edges": int(sum(g.m for g in graphs)),
-            "cliques": str(cliques), "ms_batch": batch_s * 1e3, "ms_one_per_launch": single_s * 1e3,
+    picked = collections.Counter(json.dumps(c, sort_keys=True) for c in choices)
+    line = {"metric": "batched k-clique queries/s", "workload": "batch", "value": len(ks) / min(batch_s, tuned_s),
+            "unit": "queries/s", "one_query_per_launch": len(ks) / single_s, "default_batch": len(ks) / batch_s,
+            "tuned_batch": len(ks) / tuned_s, "speedup": single_s / min(batch_s, tuned_s),
+            "speedup_tuned_vs_default": batch_s / tuned_s, "results_identical": same,
+            "k-cliques/s": cliques / min(batch_s, tuned_s), "n_graphs": len(ks),
+            "edges": int(sum(g.m for g in graphs)), "cliques": str(cliques),
+            "ms_batch": batch_s * 1e3, "ms_tuned": tuned_s * 1e3, "ms_one_per_launch": single_s * 1e3,
+            "tuned_choices": dict(picked.most_common(6)), "tune_s": tune_s, "shape_keys": len(tuner.cache),
             "prepare_s": prep_s, "generate_s": gen_s, "steps": args.steps, "warmup": args.warmup,
             "config": {"graphs": "G(n,p), n~U{64..4096}, avg degree U[8,64], 1-4 planted cliques U{8..24}, "
-                                 "k~U{3..10}, seed 0"}}
+                                 "k~U{3..10}, seed 0", "checksum": True}}
     print(json.dumps(line), flush=True)
 
 

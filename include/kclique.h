@@ -88,7 +88,9 @@ typedef struct {
     uint64_t *d_edge_cycles;   /* optional device [m]: SM clock cycles the warps spent on e's sub-branch */
     uint32_t split_min;        /* k >= 7: sub-branches with |VSet| >= split_min are split across warps,
                                   one work item per top-frame vertex (0 = 64; 0xFFFFFFFF = never) */
-    uint32_t pad;
+    uint32_t width_min;        /* bitset width class: sub-branches of fewer than 32 * width_min vertices
+                                  run in the kernels for width_min words (1, 2, 4, 8, 16, 32; 0 = the
+                                  narrowest that holds them) */
     uint64_t ticket_begin;     /* run only the top-level edges [ticket_begin, ticket_end) of the order by */
     uint64_t ticket_end;       /* |VSet| descending (0, 0 = all): a shard for one of several GPUs */
 } kc_params;
@@ -186,6 +188,14 @@ KC_API kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32
                               const kc_params *p, kc_stream s, kc_result *results);
 
 /*
+ * kclique_count_batch_tuned -- kclique_count_batch with per-query choices: qp[i] (when qp
+ * is not NULL) gives t_max, split_min and width_min of query i (an autotuner's picks);
+ * flags, blocks and warps_per_block come from p.  Results as for kclique_count_batch.
+ */
+KC_API kc_status kclique_count_batch_tuned(const kc_graph *const *graphs, const uint32_t *ks, const kc_params *qp,
+                                           uint32_t nq, const kc_params *p, kc_stream s, kc_result *results);
+
+/*
  * kclique_count_batch_noalloc -- the batched count of kclique_count_batch for callers
  * that cannot allocate device memory when they count (a fixed pre-reserved pool, a
  * driver-thread callback, a process at its memory limit).  The paper has no
@@ -225,7 +235,9 @@ typedef struct kc_server kc_server;
 
 /* The calls the server makes.  NULL in kc_server_config = this library on the GPU
  * (kclique_prepare / kclique_count_batch with KC_CHECKSUM / kclique_list with
- * KC_ROWS_ONLY into a device buffer copied to `rows` / kclique_release).  A caller may
+ * KC_ROWS_ONLY into a device buffer copied to `rows` / kclique_release).  count_batch's
+ * qp[i] holds the per-request choices of kc_request (t_max, split_min, width_min; 0 =
+ * the server's kc_server_config.params).  A caller may
  * pass stand-ins to exercise the scheduling without a GPU.  Graph handles are opaque
  * to the server.  list: write up to cap rows of k ids to the HOST buffer rows (may be
  * NULL) and return KC_TRUNCATED with r->written == cap when the buffer filled (totals
@@ -234,7 +246,8 @@ typedef struct {
     void *ctx;
     kc_status (*prepare)(void *ctx, const uint32_t *row_ptr, const uint32_t *col, uint32_t n, uint64_t nnz,
                          void **graph, uint64_t *resident_bytes);
-    kc_status (*count_batch)(void *ctx, void *const *graphs, const uint32_t *ks, uint32_t nq, kc_result *results);
+    kc_status (*count_batch)(void *ctx, void *const *graphs, const uint32_t *ks, const kc_params *qp, uint32_t nq,
+                             kc_result *results);
     kc_status (*list)(void *ctx, void *graph, uint32_t k, uint32_t *rows, uint64_t cap, kc_result *r);
     void (*release)(void *ctx, void *graph);
 } kc_server_backend;
@@ -265,6 +278,9 @@ typedef struct {
     uint32_t n;
     uint32_t pin;             /* upload: never evicted */
     uint64_t nnz;
+    uint32_t t_max, split_min, width_min;  /* count: this request's choices (an autotuner's picks);
+                                              0 = the server's params */
+    uint32_t pad;
 } kc_request;
 
 typedef struct {

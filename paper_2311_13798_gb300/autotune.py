@@ -1,16 +1,22 @@
 """Autotuner for the branch kernels' launch parameters.
 
-Tuned knobs (all leave results unchanged, only speed):
-  * split_min -- sub-branches with |VSet| >= split_min are split into per-vertex work
-    items spread over all warps (the depth-1 split of heavy branches, k >= 7);
-  * t_max     -- early termination on cliques only (1) or on cliques and 2-plexes (2);
-  * blocks    -- persistent grid size (0 = one full wave of resident blocks).
-The bitset width class is not a knob: it follows from each sub-branch's size.
+Tuned knobs (every value gives the same counts and checksums, only the speed changes):
+  * t_max      -- early termination on cliques (1), 2-plexes (2) or 3-plexes (3), or the
+                  paper's rule (0: t = 2 if k <= tau/2, else 3);
+  * split_min  -- sub-branches with |VSet| >= split_min are split across the warps of a
+                  block, one work item per top-frame vertex (k >= 7; 0xFFFFFFFF = never);
+  * width_min  -- the narrowest bitset width class used: a sub-branch that fits fewer
+                  words runs in the kernels for width_min words;
+  * warps_per_block -- warps that share one split sub-branch's frame (1..4).
+Per-query knobs (t_max, split_min, width_min) go to kclique_count_batch_tuned and to the
+server's requests; warps_per_block is a launch-wide knob of kclique_count.
 
-A candidate is timed on a bounded shard of the ticket order (the heaviest tickets
-first, which dominate the run time), so tuning costs a small fraction of one query.
-Choices are cached in a JSON file keyed by device name, a coarse shape of the graph
-(edge count and tau buckets) and k.
+A candidate is timed on a bounded shard of the ticket order (the heaviest tickets,
+which dominate the run time), so tuning costs a small fraction of one query.  The
+search is coordinate descent: one knob at a time, from the library defaults, keeping a
+change only when it is faster by more than `margin`.  Choices are cached per device,
+coarse graph shape (edge count and tau, in powers of two) and k, in memory and, with
+`cache_path`, in a JSON file.
 """
 from __future__ import annotations
 
@@ -20,10 +26,12 @@ import os
 import threading
 
 DEFAULT_GRID = {
-    "split_min": [64, 48, 128, 0xFFFFFFFF],
-    "t_max": [2, 1],
-    "blocks": [0],
+    "t_max": [0, 2, 3, 1],
+    "split_min": [0, 32, 128, 0xFFFFFFFF],
+    "width_min": [0, 2, 4],
+    "warps_per_block": [0, 2],
 }
+PER_QUERY = ("t_max", "split_min", "width_min")
 
 
 def shape_key(info: dict, k: int, device: str) -> str:
@@ -34,14 +42,17 @@ def shape_key(info: dict, k: int, device: str) -> str:
 
 class Autotuner:
     def __init__(self, cache_path: str | None = None, grid: dict | None = None, shard: int = 512,
-                 timer=None, device_name: str | None = None):
+                 timer=None, device_name: str | None = None, margin: float = 0.03, reps: int = 2):
         self.cache_path = cache_path
         self.grid = grid or DEFAULT_GRID
         self.shard = shard
         self.timer = timer            # callable(handle, k, params) -> ms; default: the library
         self.device_name = device_name
+        self.margin = margin
+        self.reps = reps
         self.lock = threading.Lock()
         self.cache = {}
+        self.infos = {}
         if cache_path and os.path.exists(cache_path):
             with open(cache_path) as f:
                 self.cache = json.load(f)
@@ -59,38 +70,49 @@ class Autotuner:
         if self.timer is not None:
             return float(self.timer(h, k, params))
         from . import kclique as K
-        r = K.kclique_count(h, k, ticket_begin=0, ticket_end=self.shard, **params)
-        return float(r["ms_count"])
+        best = None
+        for _ in range(self.reps):
+            r = K.kclique_count(h, k, ticket_begin=0, ticket_end=self.shard, **params)
+            best = r["ms_count"] if best is None else min(best, r["ms_count"])
+        return float(best)
 
-    def candidates(self):
-        for sm in self.grid["split_min"]:
-            for t in self.grid["t_max"]:
-                for b in self.grid["blocks"]:
-                    yield {"split_min": sm, "t_max": t, "blocks": b}
+    def _info(self, h) -> dict:
+        key = getattr(h, "handle", id(h))
+        if key not in self.infos:
+            from . import kclique as K
+            self.infos[key] = K.kclique_info(h)
+        return self.infos[key]
 
     def tune(self, h, k: int, info: dict | None = None, force: bool = False) -> dict:
         """Best parameters for (graph, k); measured once per shape key, then cached."""
-        if info is None:
-            from . import kclique as K
-            info = K.kclique_info(h)
+        info = info if info is not None else self._info(h)
         key = shape_key(info, k, self._device())
         with self.lock:
             if not force and key in self.cache:
                 return dict(self.cache[key]["params"])
-        results = []
-        for p in self.candidates():
-            if k < 7 and p["split_min"] != self.grid["split_min"][0]:
-                continue  # splitting only applies to k >= 7
-            self._time(h, k, p)                # warm-up
-            results.append((self._time(h, k, p), p))
-        results.sort(key=lambda x: x[0])
-        best_ms, best = results[0]
+        best = {name: vals[0] for name, vals in self.grid.items()}
+        self._time(h, k, best)  # warm-up (module loading, first launches)
+        best_ms = self._time(h, k, best)
+        tried = [{"ms": best_ms, **best}]
+        for name, vals in self.grid.items():
+            if name == "split_min" and k < 7:
+                continue  # splitting applies to k >= 7 only
+            for v in vals[1:]:
+                cand = dict(best, **{name: v})
+                ms = self._time(h, k, cand)
+                tried.append({"ms": ms, **cand})
+                if ms < best_ms * (1.0 - self.margin):
+                    best, best_ms = cand, ms
         with self.lock:
-            self.cache[key] = {"params": best, "ms": best_ms,
-                               "tried": [{"ms": ms, **p} for ms, p in results]}
+            self.cache[key] = {"params": best, "ms": best_ms, "tried": tried}
             if self.cache_path:
                 tmp = self.cache_path + ".tmp"
                 with open(tmp, "w") as f:
                     json.dump(self.cache, f, indent=1, sort_keys=True)
                 os.replace(tmp, self.cache_path)
         return dict(best)
+
+    def choice(self, h, k: int, info: dict | None = None) -> dict:
+        """The per-query part of the tuned parameters (t_max, split_min, width_min)."""
+        p = self.tune(h, k, info)
+        return {name: p[name] for name in PER_QUERY if name in p}

@@ -101,6 +101,7 @@ kc_status run_one(const kc_graph *g, u32 k, const kc_params *p, cudaStream_t s, 
     cfg.d_edge_checksum = p ? p->d_edge_checksum : nullptr;
     cfg.d_edge_cycles = p ? p->d_edge_cycles : nullptr;
     cfg.split_min = p ? p->split_min : 0u;
+    cfg.width_min = p ? p->width_min : 0u;
     cfg.ticket_begin = p ? p->ticket_begin : 0ull;
     cfg.ticket_end = p ? p->ticket_end : 0ull;
     kc_dev_acc acc;
@@ -227,6 +228,11 @@ const char *kclique_status_string(kc_status st) {
 
 kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32_t *ks, uint32_t nq, const kc_params *p,
                               kc_stream sv, kc_result *results) {
+    return kclique_count_batch_tuned(graphs, ks, nullptr, nq, p, sv, results);
+}
+
+kc_status kclique_count_batch_tuned(const kc_graph *const *graphs, const uint32_t *ks, const kc_params *qp,
+                                    uint32_t nq, const kc_params *p, kc_stream sv, kc_result *results) {
     if (!graphs || !ks || !results) return KC_ERR_INVALID_ARG;
     if (p && (p->d_edge_count || p->d_edge_checksum || p->d_edge_cycles)) return KC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)sv;
@@ -247,6 +253,11 @@ kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32_t *ks,
         q.k = ks[i];
         q.ticket_begin = 0;
         q.ticket_end = 0;
+        if (qp) {
+            q.t_max = qp[i].t_max;
+            q.split_min = qp[i].split_min;
+            q.width_min = qp[i].width_min;
+        }
         qv.push_back(q);
         idx.push_back(i);
     }
@@ -259,6 +270,7 @@ kc_status kclique_count_batch(const kc_graph *const *graphs, const uint32_t *ks,
     cfg.warps_per_block = p ? p->warps_per_block : 0u;
     cfg.blocks = p ? p->blocks : 0u;
     cfg.split_min = p ? p->split_min : 0u;
+    cfg.width_min = p ? p->width_min : 0u;
     std::vector<kc_dev_acc> acc(qv.size());
     float ms = 0.f, msb = 0.f;
     kc_status st = kc_run_queries(qv.data(), (u32)qv.size(), &cfg, s, acc.data(), &ms, &msb);

@@ -119,19 +119,27 @@ using namespace kcb;
 // number of edges of g with |VSet| >= x (tickets are sorted by |VSet| descending)
 u64 suffix_count(const kc_graph *g, u64 x) { return x > g->tau ? 0ull : g->h_size_suffix[x]; }
 
-// smallest sub-branch size of width class W for queries at k
-u64 class_low(int W, u32 k) {
-    u64 s_lo = (W == 1) ? 0ull : 16ull * W + 1;
+// the width class (a power of two, 1..32) that a requested width_min selects
+u32 width_floor(u32 wmin) {
+    u32 w = 1;
+    while (w < wmin && w < 32) w <<= 1;
+    return w;
+}
+
+// smallest sub-branch size of width class W for queries at k; classes narrower than
+// wmin are empty and class wmin takes every smaller sub-branch
+u64 class_low(int W, u32 k, u32 wmin = 1) {
+    u64 s_lo = (W == 1 || (u32)W == width_floor(wmin)) ? 0ull : 16ull * W + 1;
     return s_lo < (u64)k - 2 ? (u64)k - 2 : s_lo;
 }
 
 // The tickets [b, en) of one query whose sub-branches fit width class W.
-void class_range(const kc_graph *g, u32 k, int W, const kc_run_cfg *cfg, u64 *b, u64 *en) {
+void class_range(const kc_graph *g, u32 k, int W, const kc_run_cfg *cfg, u64 *b, u64 *en, u32 wmin = 1) {
     auto suffix = [&](u64 x) -> u64 { return suffix_count(g, x); };
     const u64 s_hi = 32ull * W;
-    const u64 s_lo = class_low(W, k);
+    const u64 s_lo = class_low(W, k, wmin);
     *b = *en = 0;
-    if (s_lo > s_hi) return;
+    if ((u32)W < width_floor(wmin) || s_lo > s_hi) return;
     u64 bb = suffix(s_hi + 1), ee = suffix(s_lo);
     if (cfg && cfg->ticket_end > cfg->ticket_begin) {  // shard
         bb = std::max<u64>(bb, cfg->ticket_begin);
@@ -189,15 +197,19 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
                 const kc_graph *g = qv[i].g;
                 const u32 k = qv[i].k;
                 if (!cfg->list && (int)(k & 1u) != (par == 0 ? 1 : 0)) continue;
+                // per-query choices override the run's
+                const u32 t_max = qv[i].t_max ? qv[i].t_max : cfg->t_max;
+                const u32 split_min = qv[i].split_min ? qv[i].split_min : cfg->split_min;
+                const u32 wmin = qv[i].width_min ? qv[i].width_min : (cfg->width_min ? cfg->width_min : 1u);
                 u64 b, en;
-                class_range(g, k, W, cfg, &b, &en);
+                class_range(g, k, W, cfg, &b, &en, wmin);
                 if (en <= b) continue;
-                QDesc d = make_desc(g, k, cfg->t_max, b, en, nullptr);
+                QDesc d = make_desc(g, k, t_max, b, en, nullptr);
                 d.acc = (kc_dev_acc *)(uintptr_t)i;  // index for now: the device address is set below
                 // split the heavy tickets (|VSet| >= split_min) of k >= 7 queries (A12)
-                const u64 smin = cfg->split_min ? cfg->split_min : 64ull;
-                if (k >= 7 && cfg->split_min != ~0u && !cfg->list) {
-                    const u64 hb = suffix_count(g, std::max<u64>(smin, class_low(W, k)));
+                const u64 smin = split_min ? split_min : 64ull;
+                if (k >= 7 && split_min != ~0u && !cfg->list) {
+                    const u64 hb = suffix_count(g, std::max<u64>(smin, class_low(W, k, wmin)));
                     d.nheavy = hb > b ? std::min<u64>(hb - b, d.nt) : 0ull;
                 }
                 d.edge_count = cfg->d_edge_count;
@@ -241,8 +253,8 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
     a.binom = g_tables[dev];
     a.prof = (KC_SECTION_PROFILE && getenv("KC_PROFILE")) ? 1u : 0u;
     if (a.prof) {
-        KC_CUDA(cudaMallocAsync(&a.l3hist, 16 * sizeof(unsigned long long), s));
-        KC_CUDA(cudaMemsetAsync(a.l3hist, 0, 16 * sizeof(unsigned long long), s));
+        KC_CUDA(cudaMallocAsync(&a.l3hist, 64 * sizeof(unsigned long long), s));
+        KC_CUDA(cudaMemsetAsync(a.l3hist, 0, 64 * sizeof(unsigned long long), s));
     }
     std::vector<cudaEvent_t> ev(2 * groups.size() + 2);
     for (cudaEvent_t &e : ev) KC_CUDA(cudaEventCreate(&e));
@@ -294,11 +306,14 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
             for (u32 j = 0; j < nq; j++) t += h_acc[j].sec[i];
             fprintf(stderr, "[kclique] section %-10s %.3e warp-cycles\n", names[i], (double)t);
         }
-        unsigned long long hh[16];
+        unsigned long long hh[64];
         if (a.l3hist && cudaMemcpy(hh, a.l3hist, sizeof(hh), cudaMemcpyDeviceToHost) == cudaSuccess) {
             const char *bn[7] = {"<=8", "<=16", "<=32", "<=64", "<=128", "<=256", ">256"};
             for (int i = 0; i < 7; i++)
                 fprintf(stderr, "[kclique] l3 frames %-5s %12llu  %.3e warp-cycles\n", bn[i], hh[i], (double)hh[8 + i]);
+            for (int i = 0; i <= 10; i++)
+                fprintf(stderr, "[kclique] l3 density %2d/10 %12llu  %.3e warp-cycles  mean size %.1f\n", i, hh[16 + i],
+                        (double)hh[27 + i], hh[16 + i] ? (double)hh[38 + i] / (double)hh[16 + i] : 0.0);
         }
     }
     if (a.l3hist) cudaFreeAsync(a.l3hist, s);

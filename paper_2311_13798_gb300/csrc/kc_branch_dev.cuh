@@ -46,6 +46,9 @@
 #ifndef KC_ITEM_MINB8  // resident blocks per SM asked of the compiler, item kernel, W = 8
 #define KC_ITEM_MINB8 6   // (6: 80 registers; 8 % faster than 4 on the power-law k = 7 run)
 #endif
+#ifndef KC_LANE_L3       // count modes, W <= 8: l = 3 children whose complement has at most
+#define KC_LANE_L3 2      // KC_LANE_L3 * |C'| missing pairs are counted in their lane (0: off)
+#endif
 #ifndef KC_LANE_ET_MAX  // l = 3 children up to this size get the in-lane plex test; larger ones
 #define KC_LANE_ET_MAX 1024  // go to the warp routine, which tests them too
 #endif
@@ -370,6 +373,22 @@ __device__ __forceinline__ int select_bit(const u32 (&cw)[W], int i) {
         before += p;
     }
     return pos;
+}
+
+// positions of the set bits of a W-word set held in registers, in increasing order, to
+// out[0 .. popc): one ballot-free pass per word (lane j stores bit j of the word at its
+// rank among the word's set bits)
+template <int W>
+__device__ __forceinline__ void compact_positions(const u32 (&cw)[W], uint16_t *out, int lane) {
+    int base = 0;
+    const u32 below = (1u << lane) - 1u;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        const u32 word = cw[w];
+        if ((word >> lane) & 1u) out[base + __popc(word & below)] = (uint16_t)(w * 32 + lane);
+        base += __popc(word);
+    }
+    __syncwarp();
 }
 
 // permute positions: new position r holds old position ord[r] (ord in L.aux2), rows and columns,
@@ -848,15 +867,15 @@ __device__ KC_COLD bool early_terminate(const Lay &L, const Args &a, const u32 *
     if (!et_allowed) return false;
     // degrees inside C, lane per vertex (early exit as soon as some vertex is too sparse)
     int mind = cnt;
+    compact_positions<W>(cw, L.aux2, lane);
     for (int base = 0; base < cnt; base += 32) {
         int i = base + lane;
         int d = cnt;
         if (i < cnt) {
-            int x = select_bit<W>(cw, i);
+            int x = L.aux2[i];
             d = 0;
 #pragma unroll
             for (int w = 0; w < W; w++) d += __popc(L.A[x * (W + KC_ROW_PAD) + w] & cw[w]);
-            L.aux2[i] = (uint16_t)x;
             L.aux[i] = (uint16_t)d;
             acc.ops += 2u * (u32)ws;
         }
@@ -960,7 +979,9 @@ __device__ __forceinline__ void poly3_warp_product(u64 &p1, u64 &p2, u64 &p3) {
 }
 
 template <int W, bool SUM>
-__device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, int tmax, bool use_et, int ws, u64 P) {
+// prof_bin (profiling builds): the density decile of the frame (10 = closed as a plex)
+__device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, int tmax, bool use_et, int ws, u64 P,
+                               int *prof_bin = nullptr) {
     u32 cw[W];
     int cnt = 0;
 #pragma unroll
@@ -972,14 +993,14 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
     u64 sumdeg = 0, sc2 = 0;
     int mind = cnt, nuni = 0;
     u64 Z = 0, q1 = 0, q2 = 0, q3 = 0;  // SUM: sum of keys, lane's part of prod (1 + z x)
+    compact_positions<W>(cw, L.aux2, lane);
     for (int base = 0; base < cnt; base += 32) {
         const int i = base + lane;
         if (i < cnt) {
-            const int x = select_bit<W>(cw, i);
+            const int x = L.aux2[i];
             int d = 0;
 #pragma unroll
             for (int w = 0; w < W; w++) d += __popc(L.A[x * (W + KC_ROW_PAD) + w] & cw[w]);
-            L.aux2[i] = (uint16_t)x;
             L.aux[i] = (uint16_t)d;
             const int db = cnt - 1 - d;
             sumdeg += (u64)d;
@@ -1038,6 +1059,7 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
         if (lane == 0) { acc.leaf += add; acc.et++; }
         return;
     }
+    if (KC_SECTION_PROFILE && prof_bin) *prof_bin = (int)((10 * E) / (c * (c - 1) / 2 + 1));
     const bool comp = M < E;
     const u32 cm = comp ? 0xFFFFFFFFu : 0u;  // rows are read as A ^ cm: the complement side flips them
     u64 t = 0, zsum = 0;
@@ -1046,13 +1068,9 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
         if (i < cnt) {
             const int x = L.aux2[i];
             u32 row[W];
-            u32 ops = 0;  // word-ops of this row's intersections (3 per word from y's word on)
+            u32 words = 0;  // words of this row's intersections (from y's word on)
 #pragma unroll
-            for (int w = 0; w < W; w++) {
-                row[w] = (L.A[x * (W + KC_ROW_PAD) + w] ^ cm) & cw[w] & gt_mask(x, w);
-                ops += 3u * (u32)__popc(row[w]) * (u32)(ws - w);
-            }
-            acc.ops += ops;
+            for (int w = 0; w < W; w++) row[w] = (L.A[x * (W + KC_ROW_PAD) + w] ^ cm) & cw[w] & gt_mask(x, w);
             const u64 zx = SUM ? L.z[x] : 0ull;
             if (SUM && comp) {
                 // z_x e2(keys of all non-neighbours of x in C)
@@ -1093,8 +1111,10 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
                         if (comp) zsum -= zx * zy * (Z - zx - zy) + zx * zy * zw;  // missing pair, complement triangles
                         else zsum += zx * zy * zw;
                     }
+                    words += (u32)(ws - (y >> 5));
                 }
             }
+            acc.ops += 3u * words;
         }
     }
     if (SUM) {
@@ -1246,14 +1266,20 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
             if (!EVEN && l == 3 && (!LIST || full)) {
                 const long long tf = (KC_SECTION_PROFILE && prof) ? clock64() : 0;
                 KC_SEC_BEGIN();
-                frame_l3_count<W, SUM>(L, C, lane, acc, min(tq, 2), use_et, Ws, P);
+                int dbin = 10;
+                frame_l3_count<W, SUM>(L, C, lane, acc, min(tq, 2), use_et, Ws, P, &dbin);
                 KC_SEC_END(3);
                 if (KC_SECTION_PROFILE && prof && a.l3hist) {
                     const int c = warp_popc<W>(C, lane);
                     if (lane == 0) {
                         const int b = c <= 8 ? 0 : c <= 16 ? 1 : c <= 32 ? 2 : c <= 64 ? 3 : c <= 128 ? 4 : c <= 256 ? 5 : 6;
+                        const unsigned long long dt = (unsigned long long)(clock64() - tf);
                         atomicAdd(&a.l3hist[b], 1ull);
-                        atomicAdd(&a.l3hist[8 + b], (unsigned long long)(clock64() - tf));
+                        atomicAdd(&a.l3hist[8 + b], dt);
+                        // by edge density decile (10: closed as a plex): frames, cycles, vertices
+                        atomicAdd(&a.l3hist[16 + dbin], 1ull);
+                        atomicAdd(&a.l3hist[27 + dbin], dt);
+                        atomicAdd(&a.l3hist[38 + dbin], (unsigned long long)c);
                     }
                 }
                 phase = 3;
@@ -1519,8 +1545,78 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                         closed = true;
                     }
                 }
+                if (!SUM && KC_LANE_L3 > 0 && W <= 8 && !EVEN && !closed && l2 == 3 && has && cc >= 3) {
+                    // l = 3 child counted in this lane through its complement H (exact for any
+                    // child): with dbar(x) the non-neighbours of x in C', M = sum dbar / 2 the
+                    // missing pairs and T the triangles of H,
+                    //     #triangles = C(c,3) - M (c-2) + sum_x C(dbar(x), 2) - T.
+                    // The lane gives up once M passes KC_LANE_L3 * |C'| (a dense complement:
+                    // the child goes to the warp routine).  A child whose H has maximum degree
+                    // <= t_max - 1 is a t-plex: the paper's early termination (Sec. 5).
+                    const int w0 = cv >> 5;  // the child's set has no bits below v's word
+                    const u32 budget = 2u * (u32)KC_LANE_L3 * (u32)cc;
+                    u32 msum = 0, visited = 0;
+                    u64 s2 = 0;
+                    int maxdb = 0;
+                    u32 d2[W];  // vertices with at least two missing partners
+#pragma unroll
+                    for (int w = 0; w < W; w++) d2[w] = 0u;
+#pragma unroll
+                    for (int w = 0; w < W; w++) {
+                        u32 bits = cw[w];
+                        while (bits && msum <= budget) {
+                            const int b = __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            const int x = w * 32 + b;
+                            int dg = 0;
+#pragma unroll
+                            for (int w2 = 0; w2 < W; w2++)
+                                if (w2 >= w0) dg += __popc(L.A[x * (W + KC_ROW_PAD) + w2] & cw[w2]);
+                            const int db = cc - 1 - dg;
+                            msum += (u32)db;
+                            s2 += (u64)(db * (db - 1) / 2);
+                            maxdb = max(maxdb, db);
+                            if (db >= 2) d2[w] |= 1u << b;
+                            visited++;
+                        }
+                    }
+                    acc.ops += 2u * (u32)(Ws - w0) * visited;
+                    if (msum <= budget) {
+                        // T: complement triangles x < y < z; x has two missing partners
+                        u64 tc = 0;
+                        u32 words = 0;
+#pragma unroll
+                        for (int w = 0; w < W; w++) {
+                            while (d2[w]) {
+                                const int x = w * 32 + __ffs(d2[w]) - 1;
+                                d2[w] &= d2[w] - 1;
+                                u32 r[W];  // missing partners of x above x
+#pragma unroll
+                                for (int w2 = 0; w2 < W; w2++)
+                                    r[w2] = (w2 >= w) ? (cw[w2] & ~L.A[x * (W + KC_ROW_PAD) + w2] & gt_mask(x, w2)) : 0u;
+#pragma unroll
+                                for (int wy = 0; wy < W; wy++) {
+                                    while (r[wy]) {
+                                        const int y = wy * 32 + __ffs(r[wy]) - 1;
+                                        r[wy] &= r[wy] - 1;
+#pragma unroll
+                                        for (int w2 = 0; w2 < W; w2++)
+                                            if (w2 >= wy) tc += __popc(r[w2] & ~L.A[y * (W + KC_ROW_PAD) + w2]);
+                                        words += (u32)(Ws - wy);
+                                    }
+                                }
+                            }
+                        }
+                        acc.ops += 3u * words;
+                        const u64 c = (u64)cc, m = (u64)(msum / 2);
+                        acc.leaf += c * (c - 1) * (c - 2) / 6 - m * (c - 2) + s2 - tc;
+                        if (use_et && maxdb <= tq - 1) acc.et++;
+                        acc.nodes++;
+                        closed = true;
+                    }
+                }
                 if (!EVEN && !closed && l2 == 3 && has && cc >= 3 && cc <= KC_LANE_ET_MAX && use_et &&
-                    (!LIST || full)) {
+                    (!LIST || full) && (SUM || KC_LANE_L3 == 0 || W > 8)) {
                     // l = 3 child: the t-plex test and the Alg. 6 count in this lane (a lane
                     // leaves the test at its first vertex of too small degree); SUM: the x^3
                     // coefficient of prod (1 + c x), c = z_f (universal) or z_a + z_b (pair)
@@ -1557,7 +1653,7 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                             }
                         }
                     }
-                    acc.ops += 2u * (u32)(Ws - w0) * (u32)cc;
+                    acc.ops += 2u * (u32)(Ws - w0) * (u32)cc;  // (the test may stop early)
                     if (plex) {
                         const u64 c = (u64)cc, f = (u64)nuni, pp = (c - f) / 2;
                         acc.leaf += f * (f - 1) * (f - 2) / 6 + (f * (f - 1) / 2) * pp * 2 + f * (pp * (pp - 1) / 2) * 4 +

@@ -73,6 +73,8 @@ struct kc_query {
     u32 k;
     u64 ticket_begin;   // range of g->tickets to run
     u64 ticket_end;
+    // per-query choices (0: the run's kc_run_cfg values)
+    u32 t_max = 0, split_min = 0, width_min = 0;
 };
 
 struct kc_run_cfg {
@@ -88,6 +90,7 @@ struct kc_run_cfg {
     u64 *d_edge_checksum;
     u64 *d_edge_cycles;
     u32 split_min;      // 0: default; ~0u: never split
+    u32 width_min;      // 0: the narrowest width class that holds a sub-branch
     u64 ticket_begin, ticket_end;  // shard of the ticket order (0, 0 = all)
 };
 

@@ -70,12 +70,14 @@ kc_status gpu_prepare(void *ctx, const uint32_t *row_ptr, const uint32_t *col, u
     return KC_OK;
 }
 
-kc_status gpu_count_batch(void *ctx, void *const *graphs, const uint32_t *ks, uint32_t nq, kc_result *results) {
+kc_status gpu_count_batch(void *ctx, void *const *graphs, const uint32_t *ks, const kc_params *qp, uint32_t nq,
+                          kc_result *results) {
     GpuBackend *b = (GpuBackend *)ctx;
     KC_CUDA(cudaSetDevice(b->device));
     kc_params p = b->params;
     p.flags |= KC_CHECKSUM;
-    return kclique_count_batch((const kc_graph *const *)graphs, ks, nq, &p, (kc_stream)b->qstream, results);
+    return kclique_count_batch_tuned((const kc_graph *const *)graphs, ks, qp, nq, &p, (kc_stream)b->qstream,
+                                     results);
 }
 
 kc_status gpu_list(void *ctx, void *graph, uint32_t k, uint32_t *rows, uint64_t cap, kc_result *r) {
@@ -279,6 +281,7 @@ void query_worker(kc_server *sv) {
     std::vector<Req *> batch;
     std::vector<void *> hs;
     std::vector<uint32_t> ks;
+    std::vector<kc_params> qp;
     std::vector<kc_result> res;
     while (true) {
         sv->cv.wait(lk, [&] { return !sv->countq.empty() || (sv->stop && sv->inflight == 0); });
@@ -286,6 +289,7 @@ void query_worker(kc_server *sv) {
         batch.clear();
         hs.clear();
         ks.clear();
+        qp.clear();
         while (!sv->countq.empty() && batch.size() < sv->cfg.max_batch) {
             Req *q = sv->countq.front();
             sv->countq.pop_front();
@@ -294,6 +298,12 @@ void query_worker(kc_server *sv) {
             batch.push_back(q);
             hs.push_back(g.h);
             ks.push_back(q->r.k);
+            kc_params c;
+            memset(&c, 0, sizeof(c));
+            c.t_max = q->r.t_max ? q->r.t_max : sv->cfg.params.t_max;
+            c.split_min = q->r.split_min ? q->r.split_min : sv->cfg.params.split_min;
+            c.width_min = q->r.width_min ? q->r.width_min : sv->cfg.params.width_min;
+            qp.push_back(c);
         }
         sv->st.batches++;
         sv->st.batched_queries += batch.size();
@@ -301,7 +311,8 @@ void query_worker(kc_server *sv) {
         lk.unlock();
         res.assign(batch.size(), kc_result());
         const double t0 = now_s();
-        kc_status st = sv->be.count_batch(sv->be.ctx, hs.data(), ks.data(), (uint32_t)batch.size(), res.data());
+        kc_status st =
+            sv->be.count_batch(sv->be.ctx, hs.data(), ks.data(), qp.data(), (uint32_t)batch.size(), res.data());
         lk.lock();
         sv->st.busy_count_s += now_s() - t0;
         for (size_t i = 0; i < batch.size(); i++) {

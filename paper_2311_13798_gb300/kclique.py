@@ -38,7 +38,7 @@ KC_ROWS_ONLY = 0x10
 class KcParams(C.Structure):
     _fields_ = [("t_max", C.c_uint32), ("warps_per_block", C.c_uint32), ("blocks", C.c_uint32),
                 ("flags", C.c_uint32), ("d_edge_count", C.c_void_p), ("d_edge_checksum", C.c_void_p),
-                ("d_edge_cycles", C.c_void_p), ("split_min", C.c_uint32), ("pad", C.c_uint32),
+                ("d_edge_cycles", C.c_void_p), ("split_min", C.c_uint32), ("width_min", C.c_uint32),
                 ("ticket_begin", C.c_uint64), ("ticket_end", C.c_uint64)]
 
 
@@ -61,8 +61,8 @@ KC_REQ_UPLOAD = 2
 
 _PREPARE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32, C.c_uint64,
                           C.POINTER(C.c_void_p), C.POINTER(C.c_uint64))
-_COUNT_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32), C.c_uint32,
-                        C.POINTER(KcResult))
+_COUNT_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32), C.POINTER(KcParams),
+                        C.c_uint32, C.POINTER(KcResult))
 _LIST_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.c_uint64,
                        C.POINTER(KcResult))
 _RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -82,7 +82,8 @@ class KcServerConfig(C.Structure):
 class KcRequest(C.Structure):
     _fields_ = [("kind", C.c_uint32), ("k", C.c_uint32), ("graph", C.c_uint64), ("cap", C.c_uint64),
                 ("rows", C.c_void_p), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("n", C.c_uint32),
-                ("pin", C.c_uint32), ("nnz", C.c_uint64)]
+                ("pin", C.c_uint32), ("nnz", C.c_uint64), ("t_max", C.c_uint32), ("split_min", C.c_uint32),
+                ("width_min", C.c_uint32), ("pad", C.c_uint32)]
 
 
 class KcCompletion(C.Structure):
@@ -161,6 +162,9 @@ def _load():
             lib.kc_server_stats.argtypes = [vp, C.POINTER(KcServerCounters)]
             lib.kc_server_destroy.restype = None
             lib.kc_server_destroy.argtypes = [vp]
+            lib.kclique_count_batch_tuned.restype = C.c_int
+            lib.kclique_count_batch_tuned.argtypes = [C.POINTER(vp), C.POINTER(u32), C.POINTER(KcParams), u32,
+                                                      C.POINTER(KcParams), vp, C.POINTER(KcResult)]
             lib.kclique_count_batch.restype = C.c_int
             lib.kclique_count_batch.argtypes = [C.POINTER(vp), C.POINTER(u32), u32, C.POINTER(KcParams), vp,
                                                 C.POINTER(KcResult)]
@@ -241,9 +245,10 @@ def kclique_prepare(row_ptr, col, n: int | None = None, stream=None) -> Graph:
 
 
 def _params(t_max=0, flags=0, blocks=0, warps_per_block=0, edge_count=None, edge_checksum=None,
-            edge_cycles=None, split_min=0, ticket_begin=0, ticket_end=0):
+            edge_cycles=None, split_min=0, ticket_begin=0, ticket_end=0, width_min=0):
     p = KcParams()
     p.split_min = split_min
+    p.width_min = width_min
     p.ticket_begin, p.ticket_end = ticket_begin, ticket_end
     p.t_max, p.flags, p.blocks, p.warps_per_block = t_max, flags, blocks, warps_per_block
     p.d_edge_count = edge_count.data_ptr() if edge_count is not None else None
@@ -302,17 +307,31 @@ def kclique_edge_data(g: Graph, stream=None) -> dict:
     return out
 
 
-def kclique_count_batch(graphs: list[Graph], ks, stream=None, **kw) -> list[dict]:
-    """Many (graph, k) count queries in one persistent launch per width class."""
+def kclique_count_batch(graphs: list[Graph], ks, stream=None, tuner=None, choices=None, **kw) -> list[dict]:
+    """Many (graph, k) count queries in one pass over the width classes.  With ``tuner``
+    (an ``autotune.Autotuner``) or explicit ``choices`` (one dict of t_max / split_min /
+    width_min per query), each query runs with its own parameters
+    (kclique_count_batch_tuned)."""
     nq = len(graphs)
-    hs = (C.c_void_p * nq)(*[g.handle for g in graphs])
-    kk = (C.c_uint32 * nq)(*[int(k) for k in ks])
-    res = (KcResult * nq)()
+    hs = (C.c_void_p * max(nq, 1))(*[g.handle for g in graphs])
+    kk = (C.c_uint32 * max(nq, 1))(*[int(k) for k in ks])
+    res = (KcResult * max(nq, 1))()
     p = _params(**kw)
-    st = _load().kclique_count_batch(hs, kk, nq, C.byref(p), _stream(stream), res)
+    if tuner is not None and choices is None:
+        choices = [tuner.choice(g, int(k)) for g, k in zip(graphs, ks)]
+    if choices is not None:
+        qp = (KcParams * max(nq, 1))(*[_params(**c) for c in choices])
+        st = _load().kclique_count_batch_tuned(hs, kk, qp, nq, C.byref(p), _stream(stream), res)
+    else:
+        st = _load().kclique_count_batch(hs, kk, nq, C.byref(p), _stream(stream), res)
     if st != KC_OK:
         raise KCliqueError(st, "kclique_count_batch")
     return [_result(res[i], KC_OK) for i in range(nq)]
+
+
+def kclique_count_batch_tuned(graphs: list[Graph], ks, choices, stream=None, **kw) -> list[dict]:
+    """kclique_count_batch with per-query choices (dicts of t_max / split_min / width_min)."""
+    return kclique_count_batch(graphs, ks, stream=stream, choices=choices, **kw)
 
 
 def kclique_int_peak(stream=None) -> dict:

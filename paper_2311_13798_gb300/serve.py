@@ -78,7 +78,7 @@ class _CallbackBackend:
             except Exception:  # surfaced as a failed upload
                 return K.KC_ERR_CUDA
 
-        def count_batch(ctx, hs, ks, nq, res):
+        def count_batch(ctx, hs, ks, qp, nq, res):
             try:
                 got = be.count_batch([self.handles[hs[i]] for i in range(nq)], [ks[i] for i in range(nq)])
                 for i, x in enumerate(got):

@@ -55,7 +55,7 @@ def test_server_structs_match_the_header():
     """The binding's server structs have the sizes of the C ones (fields of 8-byte
     alignment in the order the header gives)."""
     from paper_2311_13798_gb300 import kclique as K
-    assert ctypes.sizeof(K.KcRequest) == 4 + 4 + 8 + 8 + 8 + 8 + 8 + 4 + 4 + 8
+    assert ctypes.sizeof(K.KcRequest) == 4 + 4 + 8 + 8 + 8 + 8 + 8 + 4 + 4 + 8 + 4 * 4
     assert ctypes.sizeof(K.KcCompletion) == 8 + 8 + 4 + 4 + 4 + 4 + 8 * 4 + 8 + 8
     assert ctypes.sizeof(K.KcServerBackend) == 5 * 8
     assert ctypes.sizeof(K.KcServerConfig) == 8 + 4 + 4 + 4 + 4 + ctypes.sizeof(K.KcParams) + 8

@@ -9,13 +9,14 @@ def test_picks_fastest_and_caches(tmp_path):
 
     def timer(h, k, p):
         calls.append(dict(p))
-        return 10.0 + (p["split_min"] == 128) * -5.0 + (p["t_max"] == 1) * 3.0
+        return 10.0 + (p["split_min"] == 128) * -5.0 + (p["t_max"] == 1) * 3.0 + (p["width_min"] == 4) * -1.0
 
     path = str(tmp_path / "tune.json")
     t = Autotuner(cache_path=path, timer=timer, device_name="GB300")
     info = {"m": 10_000_000, "tau": 246}
     best = t.tune(object(), 7, info)
-    assert best == {"split_min": 128, "t_max": 2, "blocks": 0}
+    assert best == {"t_max": 0, "split_min": 128, "width_min": 4, "warps_per_block": 0}
+    assert t.choice(object(), 7, info) == {"t_max": 0, "split_min": 128, "width_min": 4}
     n = len(calls)
     assert t.tune(object(), 7, info) == best and len(calls) == n  # cached, not re-measured
     d = json.load(open(path))
@@ -34,3 +35,11 @@ def test_small_k_does_not_sweep_split():
 
     Autotuner(timer=timer, device_name="x").tune(object(), 5, {"m": 100, "tau": 3})
     assert len(seen) == 1
+
+
+def test_keeps_defaults_within_the_margin():
+    def timer(h, k, p):
+        return 10.0 - (p["t_max"] == 3) * 0.1   # 1 %: below the 3 % margin
+
+    best = Autotuner(timer=timer, device_name="x").tune(object(), 8, {"m": 100, "tau": 9})
+    assert best["t_max"] == 0

@@ -138,3 +138,80 @@ def test_config4_batch_of_uneven_graphs():
         assert (r["count"], r["checksum"]) == (want["count"], want["checksum"])
         single = K().kclique_count(h, k, flags=K().KC_CHECKSUM)
         assert (single["count"], single["checksum"]) == (r["count"], r["checksum"])
+
+
+def test_config4_batch_tuned_choices_give_identical_results():
+    """Per-query choices (t_max, split_min, width_min), picked by the autotuner or set
+    by hand, change the speed only: every query's count and checksum stays the oracle's."""
+    from paper_2311_13798_gb300.autotune import Autotuner
+    specs = G.batch_specs(count=24, seed=5, n_hi=500)
+    graphs = [G.batch_graph(s) for s in specs]
+    hs = [prep(g) for g in graphs]
+    ks = [s["k"] for s in specs]
+    want = [O.count(g, k) for g, k in zip(graphs, ks)]
+    base = K().kclique_count_batch(hs, ks, flags=K().KC_CHECKSUM)
+    assert [(r["count"], r["checksum"]) for r in base] == [(w["count"], w["checksum"]) for w in want]
+    tuner = Autotuner(shard=64, reps=1)
+    tuned = K().kclique_count_batch(hs, ks, tuner=tuner, flags=K().KC_CHECKSUM)
+    assert [(r["count"], r["checksum"]) for r in tuned] == [(w["count"], w["checksum"]) for w in want]
+    assert tuner.cache  # the tuner measured and cached its picks
+    for i, choice in enumerate([{"t_max": 3, "split_min": 3, "width_min": 4}, {"t_max": 1, "width_min": 32},
+                                {"t_max": 2, "split_min": 0xFFFFFFFF, "width_min": 2}]):
+        got = K().kclique_count_batch(hs, ks, choices=[choice] * len(hs), flags=K().KC_CHECKSUM)
+        assert [(r["count"], r["checksum"]) for r in got] == [(w["count"], w["checksum"]) for w in want], i
+
+
+@pytest.fixture(scope="module")
+def sbm_full():
+    g, info = G.sbm_2plex()
+    ref = GOLD.get("c3/graph")
+    if ref is None:
+        pytest.skip("c3/graph not computed by oracle/make_golden.py")
+    assert g.fingerprint() == ref["fingerprint"], "generator mismatch, not a parity failure"
+    blk = info["block_of"]
+    u, v = g.edges()
+    blocks = {}
+    for b in range(200):
+        keep = (blk[u] == b) & (blk[v] == b)
+        blocks[b] = prep(G.from_edges(g.n, u[keep], v[keep]))
+    return g, info, prep(g), blocks
+
+
+def test_config3_full_size_sbm(sbm_full):
+    """The dense-core SBM at full size (50,000 vertices, 200 blocks of 250), pinned as a
+    decomposition: every k-clique lies in one block or holds an inter-block edge, so
+    whole = sum of the blocks + the inter-block term (tests/golden: the 2-plex blocks by
+    the closed form at k = 6..10, the dense blocks by the oracle at k = 6, the inter-block
+    term by the oracle).  The whole graph runs at k = 6 (count and checksum against the
+    stored total) and k = 7 (against the GPU's own per-block counts and the stored
+    inter-block term; count only); each 2-plex block runs alone at k = 6..10."""
+    g, info, h, blocks = sbm_full
+    plex = GOLD["c3/plex_blocks"]["blocks"]
+    M64 = (1 << 64) - 1
+    # 2-plex blocks alone, k = 6..10, against the closed form
+    for b in info["two_plex_blocks"]:
+        for k in range(6, 11):
+            r = K().kclique_count(blocks[b], k, flags=K().KC_CHECKSUM)
+            assert [str(r["count"]), str(r["checksum"])] == plex[str(b)][str(k)], (b, k)
+    dense = [b for b in range(200) if b not in set(info["two_plex_blocks"])]
+    have6 = all(f"c3/dense{b}/k6" in GOLD for b in dense)
+    for b in dense:
+        key = f"c3/dense{b}/k6"
+        if key in GOLD:
+            r = K().kclique_count(blocks[b], 6, flags=K().KC_CHECKSUM)
+            assert (str(r["count"]), str(r["checksum"])) == (GOLD[key]["count"], GOLD[key]["checksum"]), b
+    # the whole graph at k = 6 against the sum of the stored block values
+    whole6 = K().kclique_count(h, 6, flags=K().KC_CHECKSUM)
+    if have6:
+        want_c = sum(int(plex[str(b)]["6"][0]) for b in info["two_plex_blocks"]) + \
+            sum(int(GOLD[f"c3/dense{b}/k6"]["count"]) for b in dense) + int(GOLD["c3/cross_k6"]["count"])
+        want_s = (sum(int(plex[str(b)]["6"][1]) for b in info["two_plex_blocks"]) +
+                  sum(int(GOLD[f"c3/dense{b}/k6"]["checksum"]) for b in dense) +
+                  int(GOLD["c3/cross_k6"]["checksum"])) & M64
+        assert (whole6["count"], whole6["checksum"]) == (want_c, want_s)
+    # k = 7 (count): the whole against the blocks run alone plus the stored inter-block term
+    parts = [K().kclique_count(blocks[b], 7) for b in range(200)]
+    whole7 = K().kclique_count(h, 7)
+    assert whole7["count"] == sum(p["count"] for p in parts) + int(GOLD["c3/cross_k7"]["count"])
+    for b in info["two_plex_blocks"]:
+        assert str(parts[b]["count"]) == plex[str(b)]["7"][0]

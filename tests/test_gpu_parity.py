@@ -389,5 +389,7 @@ def test_size_range_shards_add_up(cache):
             for n in (2, 3, 8):
                 parts = [K.kclique_count(h, k, ticket_begin=b, ticket_end=e, flags=K.KC_CHECKSUM)
                          for b, e in shard.partition_by_size(vs, k, n) if e > b]
-                limbs = [sum(x) for x in zip(*(shard.to_limbs(p["count"], p["checksum"]) for p in parts))]
+                limbs = [0] * 6  # no shard has work when k > tau + 2
+                for p in parts:
+                    limbs = [a + b for a, b in zip(limbs, shard.to_limbs(p["count"], p["checksum"]))]
                 assert shard.from_limbs(limbs) == (want["count"], want["checksum"]), (name, k, n)
