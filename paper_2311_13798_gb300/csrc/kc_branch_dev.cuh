@@ -46,7 +46,7 @@
 #ifndef KC_ITEM_MINB8  // resident blocks per SM asked of the compiler, item kernel, W = 8
 #define KC_ITEM_MINB8 6   // (6: 80 registers; 8 % faster than 4 on the power-law k = 7 run)
 #endif
-#ifndef KC_LANE_L3       // count modes, W <= 8: l = 3 children whose complement has at most
+#ifndef KC_LANE_L3       // W <= 8: l = 3 children whose complement has at most
 #define KC_LANE_L3 2      // KC_LANE_L3 * |C'| missing pairs are counted in their lane (0: off)
 #endif
 #ifndef KC_LANE_ET_MAX  // l = 3 children up to this size get the in-lane plex test; larger ones
@@ -480,7 +480,7 @@ struct Acc {
 
 // ---------------------------------------------------------------- A5 extraction
 template <int W>
-__device__ KC_COLD void extract(const Lay &L, const QDesc &q, int s, u32 e, u32 re, int lane, Acc &acc) {
+__device__ __forceinline__ void extract_body(const Lay &L, const QDesc &q, int s, u32 e, u32 re, int lane, Acc &acc) {
     constexpr int RS = W + KC_ROW_PAD;
     for (int i = lane; i < s * RS; i += 32) L.A[i] = 0;
     __syncwarp();
@@ -555,6 +555,19 @@ __device__ KC_COLD void extract(const Lay &L, const QDesc &q, int s, u32 e, u32 
         }
     }
     __syncwarp();
+}
+
+#ifndef KC_EXTRACT_NOINLINE  // 1: extraction out of line as well (measured slower at k = 5)
+#define KC_EXTRACT_NOINLINE 0
+#endif
+#if KC_EXTRACT_NOINLINE
+#define KC_EXTRACT_ATTR __noinline__
+#else
+#define KC_EXTRACT_ATTR __forceinline__
+#endif
+template <int W>
+__device__ KC_EXTRACT_ATTR void extract(const Lay &L, const QDesc &q, int s, u32 e, u32 re, int lane, Acc &acc) {
+    extract_body<W>(L, q, s, e, re, lane, acc);
 }
 
 // ---------------------------------------------------------------- A6 colouring
@@ -1545,11 +1558,14 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                         closed = true;
                     }
                 }
-                if (!SUM && KC_LANE_L3 > 0 && W <= 8 && !EVEN && !closed && l2 == 3 && has && cc >= 3) {
+                if (KC_LANE_L3 > 0 && W <= 8 && !EVEN && !closed && l2 == 3 && has && cc >= 3 && (!LIST || full)) {
                     // l = 3 child counted in this lane through its complement H (exact for any
                     // child): with dbar(x) the non-neighbours of x in C', M = sum dbar / 2 the
                     // missing pairs and T the triangles of H,
-                    //     #triangles = C(c,3) - M (c-2) + sum_x C(dbar(x), 2) - T.
+                    //     #triangles = C(c,3) - M (c-2) + sum_x C(dbar(x), 2) - T,
+                    // and with keys (SUM) the same identity weighted:
+                    //     e3(z_C') - sum_{ab in M} z_a z_b (Z - z_a - z_b)
+                    //              + sum_x z_x e2(z of x's non-neighbours) - T_z.
                     // The lane gives up once M passes KC_LANE_L3 * |C'| (a dense complement:
                     // the child goes to the warp routine).  A child whose H has maximum degree
                     // <= t_max - 1 is a t-plex: the paper's early termination (Sec. 5).
@@ -1557,10 +1573,11 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                     const u32 budget = 2u * (u32)KC_LANE_L3 * (u32)cc;
                     u32 msum = 0, visited = 0;
                     u64 s2 = 0;
+                    u64 e1 = 0, e2 = 0, e3 = 0;  // SUM: elementary symmetric sums of the keys
                     int maxdb = 0;
-                    u32 d2[W];  // vertices with at least two missing partners
+                    u32 dm[W];  // vertices with missing partners (SUM: one or more; else two or more)
 #pragma unroll
-                    for (int w = 0; w < W; w++) d2[w] = 0u;
+                    for (int w = 0; w < W; w++) dm[w] = 0u;
 #pragma unroll
                     for (int w = 0; w < W; w++) {
                         u32 bits = cw[w];
@@ -1576,32 +1593,64 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                             msum += (u32)db;
                             s2 += (u64)(db * (db - 1) / 2);
                             maxdb = max(maxdb, db);
-                            if (db >= 2) d2[w] |= 1u << b;
+                            if (db >= (SUM ? 1 : 2)) dm[w] |= 1u << b;
+                            if (SUM) {
+                                const u64 z = L.z[x];
+                                e3 += e2 * z;
+                                e2 += e1 * z;
+                                e1 += z;
+                            }
                             visited++;
                         }
                     }
                     acc.ops += 2u * (u32)(Ws - w0) * visited;
                     if (msum <= budget) {
-                        // T: complement triangles x < y < z; x has two missing partners
-                        u64 tc = 0;
+                        // pairs of H (x, y > x) and its triangles x < y < z
+                        u64 tc = 0, zpair = 0, znb = 0, ztri = 0;
                         u32 words = 0;
 #pragma unroll
                         for (int w = 0; w < W; w++) {
-                            while (d2[w]) {
-                                const int x = w * 32 + __ffs(d2[w]) - 1;
-                                d2[w] &= d2[w] - 1;
+                            while (dm[w]) {
+                                const int x = w * 32 + __ffs(dm[w]) - 1;
+                                dm[w] &= dm[w] - 1;
+                                const u64 zx = SUM ? L.z[x] : 0ull;
                                 u32 r[W];  // missing partners of x above x
+                                u64 f1 = 0, f2 = 0;
 #pragma unroll
-                                for (int w2 = 0; w2 < W; w2++)
-                                    r[w2] = (w2 >= w) ? (cw[w2] & ~L.A[x * (W + KC_ROW_PAD) + w2] & gt_mask(x, w2)) : 0u;
+                                for (int w2 = 0; w2 < W; w2++) {
+                                    const u32 nb = (w2 >= w0) ? (cw[w2] & ~L.A[x * (W + KC_ROW_PAD) + w2] &
+                                                                 ~((w2 == w) ? (1u << (x & 31)) : 0u)) : 0u;
+                                    r[w2] = nb & gt_mask(x, w2);
+                                    if (SUM) {  // e2 of the keys of all of x's missing partners
+                                        u32 t = nb;
+                                        while (t) {
+                                            const u64 z = L.z[w2 * 32 + __ffs(t) - 1];
+                                            t &= t - 1;
+                                            f2 += f1 * z;
+                                            f1 += z;
+                                        }
+                                    }
+                                }
+                                if (SUM) znb += zx * f2;
 #pragma unroll
                                 for (int wy = 0; wy < W; wy++) {
                                     while (r[wy]) {
                                         const int y = wy * 32 + __ffs(r[wy]) - 1;
                                         r[wy] &= r[wy] - 1;
+                                        const u64 zy = SUM ? L.z[y] : 0ull;
+                                        u64 zw = 0;
 #pragma unroll
-                                        for (int w2 = 0; w2 < W; w2++)
-                                            if (w2 >= wy) tc += __popc(r[w2] & ~L.A[y * (W + KC_ROW_PAD) + w2]);
+                                        for (int w2 = 0; w2 < W; w2++) {
+                                            if (w2 < wy) continue;
+                                            u32 tb = r[w2] & ~L.A[y * (W + KC_ROW_PAD) + w2];
+                                            tc += __popc(tb);
+                                            if (SUM)
+                                                while (tb) { zw += L.z[w2 * 32 + __ffs(tb) - 1]; tb &= tb - 1; }
+                                        }
+                                        if (SUM) {
+                                            zpair += zx * zy * (e1 - zx - zy);
+                                            ztri += zx * zy * zw;
+                                        }
                                         words += (u32)(Ws - wy);
                                     }
                                 }
@@ -1610,13 +1659,14 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                         acc.ops += 3u * words;
                         const u64 c = (u64)cc, m = (u64)(msum / 2);
                         acc.leaf += c * (c - 1) * (c - 2) / 6 - m * (c - 2) + s2 - tc;
+                        if (SUM) acc.csum += Pc * (e3 - zpair + znb - ztri);
                         if (use_et && maxdb <= tq - 1) acc.et++;
                         acc.nodes++;
                         closed = true;
                     }
                 }
                 if (!EVEN && !closed && l2 == 3 && has && cc >= 3 && cc <= KC_LANE_ET_MAX && use_et &&
-                    (!LIST || full) && (SUM || KC_LANE_L3 == 0 || W > 8)) {
+                    (!LIST || full) && (KC_LANE_L3 == 0 || W > 8)) {
                     // l = 3 child: the t-plex test and the Alg. 6 count in this lane (a lane
                     // leaves the test at its first vertex of too small degree); SUM: the x^3
                     // coefficient of prod (1 + c x), c = z_f (universal) or z_a + z_b (pair)
