@@ -55,7 +55,7 @@ def parse(argv=None):
     ap.add_argument("--no-k9", action="store_true", help="skip the k = 9 record after the timed steps")
     ap.add_argument("--k9-tickets", type=int, default=2000,
                     help="k = 9 record: the heaviest this many sub-branches (tickets [0, n))")
-    ap.add_argument("--workload", choices=["power_law", "batch", "serve", "probe"], default="power_law",
+    ap.add_argument("--workload", choices=["power_law", "batch", "serve", "probe", "ablation"], default="power_law",
                     help="power_law: the default bench line; batch / serve: the batching and serving "
                          "measurements (separate JSON lines); probe: one count on a Chung-Lu graph sized "
                          "by the --probe-* flags, the small case for profiler captures (not a bench value)")
@@ -380,6 +380,39 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ablation(args):
+    """The paper's ablations (Sec. 6.2) on the power-law graph: the top-level edge order
+    (truss-based = EBBkC-H, colour-based = EBBkC-C) and pruning Rule (2) and early
+    termination switched off, at k = 5, 7 and 8; every variant's count must agree."""
+    import numpy as np
+    import torch
+
+    from paper_2311_13798_gb300 import kclique as K
+    from synth import graphs as G
+    torch.cuda.set_device(0)
+    g = G.chung_lu()
+    rp = torch.from_numpy(g.row_ptr.astype(np.int32)).cuda()
+    col = torch.from_numpy(g.col.astype(np.int32)).cuda()
+    rows = []
+    counts = {}
+    for name, order in (("truss (EBBkC-H)", K.KC_ORDER_TRUSS), ("colour (EBBkC-C)", K.KC_ORDER_COLOUR)):
+        h = K.kclique_prepare(rp, col, g.n, ordering=order)
+        info = K.kclique_info(h)
+        for fname, fl in (("all on", 0), ("no Rule (2)", K.KC_NO_RULE2), ("no early termination", K.KC_NO_ET)):
+            for k in (5, 7, 8):
+                K.kclique_count(h, k, flags=fl)  # warm-up
+                r = K.kclique_count(h, k, flags=fl)
+                counts.setdefault(k, set()).add(r["count"])
+                rows.append({"ordering": name, "variant": fname, "k": k, "ms_branch": r["ms_branch"],
+                             "ms_prepare": r["ms_prepare"], "nodes": r["nodes"], "et_hits": r["et_hits"],
+                             "edge_branches": r["edge_branches"], "max_vset": info["tau"],
+                             "count": str(r["count"])})
+                print(json.dumps(rows[-1]), flush=True)
+        h.release()
+    print(json.dumps({"workload": "ablation", "graph": g.fingerprint(),
+                      "counts_agree": all(len(v) == 1 for v in counts.values()), "rows": len(rows)}), flush=True)
+
+
 def run_probe(args):
     """Prepare a Chung-Lu graph (n = --probe-n, max expected degree --probe-wmax, seed 0) and
     run one count at k = --probe-k; prints the count, the branch time and the work counters."""
@@ -423,6 +456,9 @@ def main(argv=None):
         return
     if args.workload == "probe":
         run_probe(args)
+        return
+    if args.workload == "ablation":
+        run_ablation(args)
         return
     import numpy as np
     import torch

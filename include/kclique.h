@@ -159,6 +159,21 @@ KC_API kc_status kclique_count(const kc_graph *g, uint32_t k, const kc_params *p
 KC_API kc_status kclique_list(const kc_graph *g, uint32_t k, uint32_t *d_out, uint64_t cap,
                        const kc_params *p, kc_stream s, kc_result *r);
 
+/*
+ * kclique_prepare_ordered -- kclique_prepare with a choice of the top-level edge order:
+ *   KC_ORDER_TRUSS  the truss-based ordering (Sec. 4.2, Eq. 6): EBBkC-H, the default;
+ *   KC_ORDER_COLOUR the colour-based ordering (Sec. 4.3, Alg. 4 lines 1-2): a greedy
+ *                   colouring of G in decreasing (degree, id) order, vertices sorted by
+ *                   non-increasing colour (ties by id), each edge branching on the common
+ *                   out-neighbours of its endpoints (EBBkC-C; the ablation of Sec. 6).
+ * Every order gives the same counts, checksums and cliques; only the work changes.
+ * KC_ERR_UNSUPPORTED if (colours + 1) * n does not fit 32 bits.
+ */
+#define KC_ORDER_TRUSS 0u
+#define KC_ORDER_COLOUR 1u
+KC_API kc_status kclique_prepare_ordered(const uint32_t *row_ptr, const uint32_t *col, uint32_t n, uint64_t nnz,
+                                         int on_device, uint32_t ordering, kc_stream s, kc_graph **out);
+
 /* kclique_info -- sizes and statistics of a prepared graph (host struct). */
 KC_API kc_status kclique_info(const kc_graph *g, kc_info *info);
 

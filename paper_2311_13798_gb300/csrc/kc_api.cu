@@ -163,7 +163,15 @@ kc_status kclique_prepare(const uint32_t *row_ptr, const uint32_t *col, uint32_t
     if (!out) return KC_ERR_INVALID_ARG;
     *out = nullptr;
     if (!row_ptr || (nnz && !col)) return KC_ERR_INVALID_ARG;
-    return kc_prepare_impl(row_ptr, col, n, nnz, on_device, (cudaStream_t)s, out);
+    return kc_prepare_impl(row_ptr, col, n, nnz, on_device, KC_ORDER_TRUSS, (cudaStream_t)s, out);
+}
+
+kc_status kclique_prepare_ordered(const uint32_t *row_ptr, const uint32_t *col, uint32_t n, uint64_t nnz,
+                                  int on_device, uint32_t ordering, kc_stream s, kc_graph **out) {
+    if (!out) return KC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!row_ptr || (nnz && !col) || ordering > KC_ORDER_COLOUR) return KC_ERR_INVALID_ARG;
+    return kc_prepare_impl(row_ptr, col, n, nnz, on_device, ordering, (cudaStream_t)s, out);
 }
 
 kc_status kclique_count(const kc_graph *g, uint32_t k, const kc_params *p, kc_stream s, kc_result *r) {

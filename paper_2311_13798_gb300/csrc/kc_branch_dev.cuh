@@ -864,11 +864,110 @@ __device__ KC_COLD bool plex3_poly(const Lay &L, const u32 (&cw)[W], int cnt, in
     return steps == cnt;
 }
 
+// the largest x in [m-1, xm) with C(x, m) <= r (C(x, m) grows with x): binary search
+__device__ __forceinline__ int colex_largest(const u128 *T, int m, int xm, u128 r) {
+    int lo = m - 1, hi = xm - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (binom(T, mid, m) <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Listing with early termination (Sec. 5.1, Alg. 6 in listing form): the l-cliques of a
+// clique or 2-plex frame are written without branching.  F = the universal vertices, P =
+// the missing pairs (a, b); a clique takes j pairs (one end of each) and l - j vertices
+// of F, so the rows number sum_j C(|F|, l-j) C(|P|, j) 2^j.  The warp reserves them in
+// one step and each lane writes the rows of its ranks: rank -> (j; an (l-j)-subset of F;
+// a j-subset of P; the ends, one bit per pair), each subset by the combinatorial number
+// system (the largest x with C(x, m) <= rank picks the m-th element).  aux2 / aux hold the
+// frame's positions and degrees; sc is scratch for the F and P lists (2 x 32W u16).
+template <int W>
+__device__ void list_plex(const Lay &L, const Args &a, const QDesc &q, const u32 *C, int cnt, int l, int d,
+                          int lane, uint16_t *sc, u128 rows) {
+    uint16_t *Fl = sc, *Pl = sc + 32 * W;  // F positions; pairs as (a, b) in Pl[2i], Pl[2i+1]
+    int nf = 0, np = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        int x = -1, y = -1;
+        bool isf = false, isp = false;
+        if (i < cnt) {
+            x = L.aux2[i];
+            isf = L.aux[i] == cnt - 1;
+            if (!isf) {
+#pragma unroll
+                for (int w = 0; w < W; w++) {
+                    const u32 nb = C[w] & ~L.A[x * (W + KC_ROW_PAD) + w] & ~((w == (x >> 5)) ? (1u << (x & 31)) : 0u);
+                    if (y < 0 && nb) y = w * 32 + __ffs(nb) - 1;
+                }
+                isp = y > x;
+            }
+        }
+        const unsigned bf = __ballot_sync(0xffffffffu, isf), bp = __ballot_sync(0xffffffffu, isp);
+        const unsigned below = (1u << lane) - 1u;
+        if (isf && KC_OK(nf + __popc(bf & below), 32 * W)) Fl[nf + __popc(bf & below)] = (uint16_t)x;
+        if (isp && KC_OK(np + __popc(bp & below), 16 * W)) {
+            Pl[2 * (np + __popc(bp & below))] = (uint16_t)x;
+            Pl[2 * (np + __popc(bp & below)) + 1] = (uint16_t)y;
+        }
+        nf += __popc(bf);
+        np += __popc(bp);
+    }
+    __syncwarp();
+    // reserve the rows (rows past the buffer are counted, not written)
+    const u64 want = rows > (u128)(1ull << 62) ? (1ull << 62) : (u64)rows;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&q.acc->written, (unsigned long long)want);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= a.cap) return;
+    const u64 nrow = min((u64)want, (u64)(a.cap - base));
+    const int npath = 2 * (d + 1);
+    for (u64 r0 = 0; r0 < nrow; r0 += 32) {
+        const u64 r = r0 + (u64)lane;
+        if (r >= nrow) continue;
+        u32 ids[KC_MAX_K];
+        for (int i = 0; i < npath; i++) ids[i] = L.path[i];
+        // j: the number of pairs the clique takes
+        u128 rem = r;
+        int j = 0;
+        u128 cj = 0;
+        for (; j <= l && j <= np; j++) {
+            cj = mul_sat(mul_sat(binom(a.binom, nf, l - j), binom(a.binom, np, j)), (u128)1 << j);
+            if (rem < cj) break;
+            rem -= cj;
+        }
+        if (j > l || j > np) continue;  // not reached: r < rows
+        const u64 ends = (u64)(rem & (((u128)1 << j) - 1));
+        rem >>= j;
+        const u128 cp = binom(a.binom, np, j);
+        u128 iB = rem % cp, iA = rem / cp;
+        int o = npath;
+        // (l - j)-subset of F: colex unranking, largest element first
+        int xm = nf;
+        for (int m = l - j; m >= 1; m--) {
+            const int x = colex_largest(a.binom, m, xm, iA);
+            iA -= binom(a.binom, x, m);
+            ids[o++] = L.vid[Fl[x]];
+            xm = x;
+        }
+        int pm = np, bit = 0;
+        for (int m = j; m >= 1; m--) {
+            const int x = colex_largest(a.binom, m, pm, iB);
+            iB -= binom(a.binom, x, m);
+            ids[o++] = L.vid[Pl[2 * x + (int)((ends >> bit) & 1ull)]];
+            bit++;
+            pm = x;
+        }
+        write_clique(a.d_out, base + r, q.k, ids, o);
+    }
+}
+
 // Returns true if the frame is closed (pruned by size or counted in closed form).
 // pr: scratch of 2 x 32W u16 (a free child slot of the next depth) for the t = 3 form
 template <int W, int MODE>
 __device__ KC_COLD bool early_terminate(const Lay &L, const Args &a, const u32 *C, int l, u64 P, int lane, Acc &acc,
-                                bool et_allowed, int ws, uint16_t *pr, int tmax) {
+                                bool et_allowed, int ws, uint16_t *pr, int tmax, const QDesc &q, int d,
+                                bool list_rows) {
     u32 cw[W];
     int cnt = 0;
 #pragma unroll
@@ -901,6 +1000,7 @@ __device__ KC_COLD bool early_terminate(const Lay &L, const Args &a, const u32 *
     u128 add = 0;
     u64 csum = 0;
     const bool want_sum = (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0;
+    if ((MODE & MODE_LIST) && list_rows && t >= 3) return false;  // listed by branching
     if (t >= 3) {
         u64 s3 = 0;
         if (!plex3_poly<W, (MODE & (MODE_CHECKSUM | MODE_LIST)) != 0>(L, cw, cnt, l, lane, pr, &add, &s3)) {
@@ -954,6 +1054,7 @@ __device__ KC_COLD bool early_terminate(const Lay &L, const Args &a, const u32 *
         csum = __shfl_sync(0xffffffffu, e, l) * P;
     }
     if (add == SAT128) acc.status |= KC_DEV_ERR_OVERFLOW;
+    if ((MODE & MODE_LIST) && list_rows) list_plex<W>(L, a, q, C, cnt, l, d, lane, pr, add);
     acc.cf = add_sat(acc.cf, add);
     acc.cf_csum += csum;
     if (lane == 0) acc.et++;
@@ -1299,8 +1400,10 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                 continue;
             }
             KC_SEC_BEGIN();
-            const bool closed = early_terminate<W, MODE>(L, a, C, l, P, lane, acc, use_et && (!LIST || full), Ws,
-                                                         (uint16_t *)(L.childC + (size_t)((d + 1) * 32) * W), tq);
+            // listing: a clique or 2-plex frame writes its rows directly (Alg. 6 listing)
+            const bool closed = early_terminate<W, MODE>(L, a, C, l, P, lane, acc, use_et, Ws,
+                                                         (uint16_t *)(L.childC + (size_t)((d + 1) * 32) * W), tq, q, d,
+                                                         LIST && !full);
             KC_SEC_END(2);
             if (closed) { phase = 3; continue; }
             if (lane == 0) { L.cur[d] = d == 0 ? u_lo - 1 : -1; L.rn[d] = 0; }
@@ -1910,7 +2013,7 @@ branch_kernel(Args a) {
                     KC_SEC_BEGIN();
                     const bool closed = early_terminate<W, MODE>(L, a, L.C0, l0, P0, lane, acc, use_et, Ws,
                                                                  (uint16_t *)(L.childC + (size_t)32 * W),
-                                                                 (int)q.t_max);
+                                                                 (int)q.t_max, q, 0, false);
                     KC_SEC_END(2);
                     const int limu = min(s, use_rule1 ? (int)L.lim[min(l0, 32 * W + 1)] : s);
                     if (closed || limu <= 0) {

@@ -63,7 +63,7 @@ struct kc_graph {
 };
 
 // ---- prepare (kc_prepare.cu)
-kc_status kc_prepare_impl(const u32 *row_ptr, const u32 *col, u32 n, u64 nnz, int on_device,
+kc_status kc_prepare_impl(const u32 *row_ptr, const u32 *col, u32 n, u64 nnz, int on_device, u32 ordering,
                           cudaStream_t s, kc_graph **out);
 void kc_free_graph(kc_graph *g);
 

@@ -672,6 +672,75 @@ __global__ void __launch_bounds__(256) peel_persistent_kernel(u64 m, const u64 *
     if (tid == 0) ps->rounds = r;
 }
 
+// ------------------------------------------------------------ colour-based ordering
+// EBBkC-C's top level (Sec. 4.3, Alg. 4 lines 1-2): a greedy colouring of G, vertices in
+// non-increasing colour (ties by id), each edge oriented to its later endpoint.  Greedy in
+// the order of decreasing (degree, id) is computed in rounds (Jones-Plassmann): a vertex
+// whose uncoloured neighbours all come later in that order takes the least colour none of
+// its coloured neighbours has.  Two such vertices are never adjacent, so a round's
+// readers never see a colour change, and the result is the sequential greedy colouring.
+// One warp per vertex; colours are found 1024 at a time in a shared bitmap.
+__device__ __forceinline__ bool colour_before(u32 du, u32 u, u32 dv, u32 v) {
+    return du > dv || (du == dv && u < v);
+}
+
+__global__ void max_kernel(const u32 *__restrict__ a, u64 n, u32 *mx) {
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(mx, a[i]);
+}
+
+__global__ void colour_round_kernel(const u32 *__restrict__ rp, const u32 *__restrict__ col, u32 n, u32 *colour,
+                                    u32 *left) {
+    __shared__ u32 bm[TPB / 32][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const u64 v64 = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (v64 >= n) return;
+    const u32 v = (u32)v64;
+    if (colour[v]) return;
+    const u32 b = rp[v], e = rp[v + 1], dv = e - b;
+    bool ready = true;
+    for (u32 i = b + lane; i < e && ready; i += 32) {
+        const u32 u = col[i];
+        if (!colour[u] && colour_before(rp[u + 1] - rp[u], u, dv, v)) ready = false;
+    }
+    ready = __all_sync(0xffffffffu, ready);
+    if (!ready) {
+        if (lane == 0) atomicAdd(left, 1u);
+        return;
+    }
+    for (u32 base = 1;; base += 1024) {  // colours [base, base + 1024)
+        bm[wib][lane] = 0;
+        __syncwarp();
+        for (u32 i = b + lane; i < e; i += 32) {
+            const u32 c = colour[col[i]];
+            if (c >= base && c < base + 1024) atomicOr(&bm[wib][(c - base) >> 5], 1u << ((c - base) & 31));
+        }
+        __syncwarp();
+        const u32 freew = ~bm[wib][lane];
+        const unsigned bal = __ballot_sync(0xffffffffu, freew != 0);
+        if (bal) {
+            const int fl = __ffs(bal) - 1;
+            const u32 wv = __shfl_sync(0xffffffffu, freew, fl);
+            if (lane == 0) colour[v] = base + 32u * (u32)fl + (u32)(__ffs(wv) - 1);
+            return;
+        }
+        __syncwarp();
+    }
+}
+
+// the edge order of the colour-based DAG: rank(a, b) = the later endpoint's position in
+// (colour descending, id ascending); ties between edges with the same later endpoint go
+// by edge id.  VSet(e) is then the common out-neighbours of e's endpoints (Alg. 4) and
+// every pair inside it comes after e.
+__global__ void colour_rank_kernel(const u32 *__restrict__ eu, const u32 *__restrict__ ev, const u32 *__restrict__ colour,
+                                   u32 cmax, u32 n, u64 m, u32 *round) {
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const u32 a = eu[i], b = ev[i];
+    const u64 pa = (u64)(cmax - colour[a]) * n + a, pb = (u64)(cmax - colour[b]) * n + b;
+    round[i] = (u32)(pa > pb ? pa : pb);
+}
+
 // ------------------------------------------------------------ VSet
 __device__ __forceinline__ bool key_less(u32 ra, u32 ea, u32 rb, u32 eb) { return ra < rb || (ra == rb && ea < eb); }
 
@@ -777,7 +846,7 @@ void kc_free_graph(kc_graph *g) {
     delete g;
 }
 
-static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u64 nnz, int on_device,
+static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u64 nnz, int on_device, u32 ordering,
                               cudaStream_t s, kc_graph *g) {
     Scratch scr;
     scr.s = s;
@@ -1002,6 +1071,35 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
     }
     if (!peeled) g->rounds = r;
 
+    // ---- EBBkC-C: the colour-based edge order replaces the truss-based one
+    if (ordering == KC_ORDER_COLOUR && m) {
+        u32 *colour, *left;
+        KC_TRY(dalloc(&colour, (u64)n + 1, s, &scr));
+        KC_TRY(dalloc(&left, 1, s, &scr));
+        KC_CUDA(cudaMemsetAsync(colour, 0, sizeof(u32) * ((u64)n + 1), s));
+        for (u64 rounds = 0;; rounds++) {
+            if (rounds > (u64)n + 1) return KC_ERR_CUDA;  // cannot happen: one vertex colours per round at least
+            KC_CUDA(cudaMemsetAsync(left, 0, sizeof(u32), s));
+            colour_round_kernel<<<warp_grid(n), TPB, 0, s>>>(g->row_ptr, g->col, n, colour, left);
+            kc_note_launch();
+            KC_CUDA(cudaMemcpyAsync(h_ctr, left, sizeof(u32), cudaMemcpyDeviceToHost, s));
+            KC_CUDA(cudaStreamSynchronize(s));
+            if (h_ctr[0] == 0) break;
+        }
+        // the largest colour: positions (cmax - colour) * n + v must fit 32 bits
+        u32 *d_cmax;
+        KC_TRY(dalloc(&d_cmax, 1, s, &scr));
+        KC_CUDA(cudaMemsetAsync(d_cmax, 0, sizeof(u32), s));
+        max_kernel<<<grid_for(n), TPB, 0, s>>>(colour, n, d_cmax);
+        kc_note_launch();
+        u32 cmax = 0;
+        KC_CUDA(cudaMemcpyAsync(&cmax, d_cmax, sizeof(u32), cudaMemcpyDeviceToHost, s));
+        KC_CUDA(cudaStreamSynchronize(s));
+        if ((u64)(cmax + 1) * n > 0xFFFFFFFFull) return KC_ERR_UNSUPPORTED;
+        colour_rank_kernel<<<grid_for(m), TPB, 0, s>>>(g->eu, g->ev, colour, cmax, n, m, g->round);
+        kc_note_launch();
+    }
+
     // ---- A4: VSet
     u32 *vcnt;
     KC_TRY(dalloc(&vcnt, m + 1, s, &scr));
@@ -1068,7 +1166,7 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
     return KC_OK;
 }
 
-kc_status kc_prepare_impl(const u32 *row_ptr, const u32 *col, u32 n, u64 nnz, int on_device, cudaStream_t s,
+kc_status kc_prepare_impl(const u32 *row_ptr, const u32 *col, u32 n, u64 nnz, int on_device, u32 ordering, cudaStream_t s,
                           kc_graph **out) {
     if (!out || (!row_ptr) || (nnz && !col)) return KC_ERR_INVALID_ARG;
     *out = nullptr;
@@ -1081,7 +1179,7 @@ kc_status kc_prepare_impl(const u32 *row_ptr, const u32 *col, u32 n, u64 nnz, in
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    kc_status st = prepare_body(row_ptr, col, n, nnz, on_device, s, g);
+    kc_status st = prepare_body(row_ptr, col, n, nnz, on_device, ordering, s, g);
     cudaEventRecord(e1, s);
     cudaStreamSynchronize(s);
     if (st == KC_OK) {

@@ -33,6 +33,8 @@ KC_NO_RULE2 = 0x2
 KC_CHECKSUM = 0x4
 KC_NO_RULE1 = 0x8
 KC_ROWS_ONLY = 0x10
+KC_ORDER_TRUSS = 0
+KC_ORDER_COLOUR = 1
 
 
 class KcParams(C.Structure):
@@ -127,6 +129,8 @@ def _load():
             vp, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
             lib.kclique_prepare.restype = C.c_int
             lib.kclique_prepare.argtypes = [vp, vp, u32, u64, C.c_int, vp, C.POINTER(vp)]
+            lib.kclique_prepare_ordered.restype = C.c_int
+            lib.kclique_prepare_ordered.argtypes = [vp, vp, u32, u64, C.c_int, u32, vp, C.POINTER(vp)]
             lib.kclique_count.restype = C.c_int
             lib.kclique_count.argtypes = [vp, u32, C.POINTER(KcParams), vp, C.POINTER(KcResult)]
             lib.kclique_list.restype = C.c_int
@@ -228,8 +232,9 @@ class Graph:
             self.handle = None
 
 
-def kclique_prepare(row_ptr, col, n: int | None = None, stream=None) -> Graph:
-    """Prepare a graph from a CSR (torch CUDA tensors, or host arrays which are copied in)."""
+def kclique_prepare(row_ptr, col, n: int | None = None, stream=None, ordering: int = 0) -> Graph:
+    """Prepare a graph from a CSR (torch CUDA tensors, or host arrays which are copied in).
+    ordering: KC_ORDER_TRUSS (EBBkC-H, default) or KC_ORDER_COLOUR (EBBkC-C's top level)."""
     rp, dev_rp, keep1 = _ptr(row_ptr)
     cp, dev_c, keep2 = _ptr(col)
     if dev_rp != dev_c:
@@ -238,10 +243,19 @@ def kclique_prepare(row_ptr, col, n: int | None = None, stream=None) -> Graph:
     nn = (nrp - 1) if n is None else int(n)
     nnz = int(keep2.numel() if hasattr(keep2, "numel") else keep2.size)
     h = C.c_void_p()
-    st = _load().kclique_prepare(rp, cp if nnz else rp, nn, nnz, dev_rp, _stream(stream), C.byref(h))
+    if ordering == KC_ORDER_TRUSS:
+        st = _load().kclique_prepare(rp, cp if nnz else rp, nn, nnz, dev_rp, _stream(stream), C.byref(h))
+    else:
+        st = _load().kclique_prepare_ordered(rp, cp if nnz else rp, nn, nnz, dev_rp, int(ordering),
+                                             _stream(stream), C.byref(h))
     if st != KC_OK:
         raise KCliqueError(st, "kclique_prepare")
     return Graph(h.value)
+
+
+def kclique_prepare_ordered(row_ptr, col, n: int | None = None, ordering: int = 0, stream=None) -> Graph:
+    """kclique_prepare with a choice of the top-level edge order (KC_ORDER_*)."""
+    return kclique_prepare(row_ptr, col, n, stream=stream, ordering=ordering)
 
 
 def _params(t_max=0, flags=0, blocks=0, warps_per_block=0, edge_count=None, edge_checksum=None,
