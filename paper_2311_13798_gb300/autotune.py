@@ -14,7 +14,8 @@ server's requests; warps_per_block is a launch-wide knob of kclique_count.
 A candidate is timed on a bounded shard of the ticket order (the heaviest tickets,
 which dominate the run time), so tuning costs a small fraction of one query.  The
 search is coordinate descent: one knob at a time, from the library defaults, keeping a
-change only when it is faster by more than `margin`.  Choices are cached per device,
+change only when it is faster by more than `margin`; a query whose shard runs in less
+than `min_ms` is launch-bound and keeps the defaults.  Choices are cached per device,
 coarse graph shape (edge count and tau, in powers of two) and k, in memory and, with
 `cache_path`, in a JSON file.
 """
@@ -42,7 +43,8 @@ def shape_key(info: dict, k: int, device: str) -> str:
 
 class Autotuner:
     def __init__(self, cache_path: str | None = None, grid: dict | None = None, shard: int = 512,
-                 timer=None, device_name: str | None = None, margin: float = 0.03, reps: int = 2):
+                 timer=None, device_name: str | None = None, margin: float = 0.03, reps: int = 2,
+                 min_ms: float = 1.0):
         self.cache_path = cache_path
         self.grid = grid or DEFAULT_GRID
         self.shard = shard
@@ -50,6 +52,7 @@ class Autotuner:
         self.device_name = device_name
         self.margin = margin
         self.reps = reps
+        self.min_ms = min_ms          # queries faster than this on the shard keep the defaults
         self.lock = threading.Lock()
         self.cache = {}
         self.infos = {}
@@ -94,7 +97,9 @@ class Autotuner:
         self._time(h, k, best)  # warm-up (module loading, first launches)
         best_ms = self._time(h, k, best)
         tried = [{"ms": best_ms, **best}]
-        for name, vals in self.grid.items():
+        # a query this short is launch-bound: its timings cannot tell the knobs apart
+        search = best_ms >= self.min_ms
+        for name, vals in (self.grid.items() if search else ()):
             if name == "split_min" and k < 7:
                 continue  # splitting applies to k >= 7 only
             for v in vals[1:]:

@@ -582,6 +582,10 @@ __device__ __forceinline__ void grid_sync(PeelState *ps) {
     __syncthreads();
 }
 
+#ifndef KC_PEEL_SOLO  // once at most this many edges remain, block 0 finishes the peel alone
+#define KC_PEEL_SOLO (1u << 15)  // (block barriers instead of grid barriers: the core's many
+#endif                           // small rounds are barrier-bound)
+
 __device__ __forceinline__ u32 vld(const u32 *p) { return *(const volatile u32 *)p; }
 __device__ __forceinline__ uint8_t vld8(const uint8_t *p) { return *(const volatile uint8_t *)p; }
 
@@ -595,10 +599,15 @@ __global__ void __launch_bounds__(256) peel_persistent_kernel(u64 m, const u64 *
                                                               const u64 *__restrict__ inc, u32 *sup, uint8_t *st,
                                                               u32 *level, u32 *round, u32 *alive, u32 *alive2,
                                                               u32 *F, u32 *Fn, PeelState *ps) {
-    const u64 tid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    const u64 nthr = (u64)gridDim.x * blockDim.x;
-    const u64 warp = tid >> 5, nwarps = nthr >> 5;
+    u64 tid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    u64 nthr = (u64)gridDim.x * blockDim.x;
+    u64 warp = tid >> 5, nwarps = nthr >> 5;
     const int lane = threadIdx.x & 31;
+    bool solo = false;  // block 0 alone: block barriers
+    auto sync = [&]() {
+        if (solo) __syncthreads();
+        else grid_sync(ps);
+    };
     u32 lvl = 0, r = 0, nf = 0, nfp = 0;
     u32 *Fp = Fn;  // previous frontier (to retire); its buffer takes the next frontier
     u64 nalive = m;
@@ -610,27 +619,37 @@ __global__ void __launch_bounds__(256) peel_persistent_kernel(u64 m, const u64 *
             nfp = 0;
             if (nalive == 0) break;
             if (tid == 0) { ps->ctr[0] = 0; ps->ctr[2] = 0xFFFFFFFFu; }
-            grid_sync(ps);
+            sync();
             for (u64 i = tid; i < nalive; i += nthr) {
                 const u32 e = vld(&alive[i]);
                 if (vld8(&st[e]) == 2) continue;
                 alive2[atomicAdd(&ps->ctr[0], 1u)] = e;
                 atomicMin(&ps->ctr[2], vld(&sup[e]));
             }
-            grid_sync(ps);
+            sync();
             nalive = vld(&ps->ctr[0]);
             const u32 minsup = vld(&ps->ctr[2]);
             u32 *t = alive; alive = alive2; alive2 = t;
             if (nalive == 0) break;
             if (minsup > lvl) lvl = minsup;
-            grid_sync(ps);  // all have read ctr[0..2]
+            sync();  // all have read ctr[0..2]
+            if (!solo && nalive <= KC_PEEL_SOLO) {
+                // every block took the same decision from the same nalive; the others leave
+                // and take no further part in any barrier
+                if (blockIdx.x != 0) return;
+                solo = true;
+                tid = threadIdx.x;
+                nthr = blockDim.x;
+                warp = tid >> 5;
+                nwarps = nthr >> 5;
+            }
             if (tid == 0) ps->ctr[1] = 0;
-            grid_sync(ps);
+            sync();
             for (u64 i = tid; i < nalive; i += nthr) {
                 const u32 e = vld(&alive[i]);
                 if (vld(&sup[e]) <= lvl) F[atomicAdd(&ps->ctr[1], 1u)] = e;
             }
-            grid_sync(ps);
+            sync();
             nf = vld(&ps->ctr[1]);
             if (nf == 0) {  // cannot happen: the least support is <= lvl
                 if (tid == 0) atomicOr(&ps->status, KC_DEV_ERR_BOUNDS);
@@ -646,7 +665,7 @@ __global__ void __launch_bounds__(256) peel_persistent_kernel(u64 m, const u64 *
             round[e] = r;
         }
         if (tid == 0) ps->cnt[(r + 1) % 3] = 0;
-        grid_sync(ps);
+        sync();
         // (B): the next frontier goes to Fp's buffer (retired above)
         u32 *const Fnext = Fp;
         u32 *const cnt = &ps->cnt[r % 3];
@@ -662,14 +681,14 @@ __global__ void __launch_bounds__(256) peel_persistent_kernel(u64 m, const u64 *
                 if (s2 == 0) { u32 old = atomicSub(&sup[e2], 1u); if (old == lvl + 1) Fnext[atomicAdd(cnt, 1u)] = e2; }
             }
         }
-        grid_sync(ps);
+        sync();
         nfp = nf;
         nf = vld(cnt);
         Fp = F;
         F = Fnext;
         r++;
     }
-    if (tid == 0) ps->rounds = r;
+    if (tid == 0 && blockIdx.x == 0) ps->rounds = r;
 }
 
 // ------------------------------------------------------------ colour-based ordering

@@ -37,6 +37,17 @@ def test_small_k_does_not_sweep_split():
     assert len(seen) == 1
 
 
+def test_short_queries_keep_the_defaults():
+    calls = []
+
+    def timer(h, k, p):
+        calls.append(p)
+        return 0.2 - (p["t_max"] == 3) * 0.1   # launch-bound: not searched
+
+    best = Autotuner(timer=timer, device_name="x").tune(object(), 8, {"m": 100, "tau": 9})
+    assert best["t_max"] == 0 and len(calls) == 2
+
+
 def test_keeps_defaults_within_the_margin():
     def timer(h, k, p):
         return 10.0 - (p["t_max"] == 3) * 0.1   # 1 %: below the 3 % margin
