@@ -712,38 +712,40 @@ __global__ void colour_round_kernel(const u32 *__restrict__ rp, const u32 *__res
                                     u32 *left) {
     __shared__ u32 bm[TPB / 32][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const u64 v64 = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (v64 >= n) return;
-    const u32 v = (u32)v64;
-    if (colour[v]) return;
-    const u32 b = rp[v], e = rp[v + 1], dv = e - b;
-    bool ready = true;
-    for (u32 i = b + lane; i < e && ready; i += 32) {
-        const u32 u = col[i];
-        if (!colour[u] && colour_before(rp[u + 1] - rp[u], u, dv, v)) ready = false;
-    }
-    ready = __all_sync(0xffffffffu, ready);
-    if (!ready) {
-        if (lane == 0) atomicAdd(left, 1u);
-        return;
-    }
-    for (u32 base = 1;; base += 1024) {  // colours [base, base + 1024)
-        bm[wib][lane] = 0;
-        __syncwarp();
-        for (u32 i = b + lane; i < e; i += 32) {
-            const u32 c = colour[col[i]];
-            if (c >= base && c < base + 1024) atomicOr(&bm[wib][(c - base) >> 5], 1u << ((c - base) & 31));
+    const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+    for (u64 v64 = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v64 < n; v64 += nwarps) {
+        const u32 v = (u32)v64;
+        if (colour[v]) continue;
+        const u32 b = rp[v], e = rp[v + 1], dv = e - b;
+        bool ready = true;
+        for (u32 i = b + lane; i < e && ready; i += 32) {
+            const u32 u = col[i];
+            if (!colour[u] && colour_before(rp[u + 1] - rp[u], u, dv, v)) ready = false;
         }
-        __syncwarp();
-        const u32 freew = ~bm[wib][lane];
-        const unsigned bal = __ballot_sync(0xffffffffu, freew != 0);
-        if (bal) {
-            const int fl = __ffs(bal) - 1;
-            const u32 wv = __shfl_sync(0xffffffffu, freew, fl);
-            if (lane == 0) colour[v] = base + 32u * (u32)fl + (u32)(__ffs(wv) - 1);
-            return;
+        ready = __all_sync(0xffffffffu, ready);
+        if (!ready) {
+            if (lane == 0) atomicAdd(left, 1u);
+            continue;
         }
-        __syncwarp();
+        for (u32 base = 1;; base += 1024) {  // colours [base, base + 1024)
+            bm[wib][lane] = 0;
+            __syncwarp();
+            for (u32 i = b + lane; i < e; i += 32) {
+                const u32 c = colour[col[i]];
+                if (c >= base && c < base + 1024) atomicOr(&bm[wib][(c - base) >> 5], 1u << ((c - base) & 31));
+            }
+            __syncwarp();
+            const u32 freew = ~bm[wib][lane];
+            const unsigned bal = __ballot_sync(0xffffffffu, freew != 0);
+            if (bal) {
+                const int fl = __ffs(bal) - 1;
+                const u32 wv = __shfl_sync(0xffffffffu, freew, fl);
+                if (lane == 0) colour[v] = base + 32u * (u32)fl + (u32)(__ffs(wv) - 1);
+                __syncwarp();
+                break;
+            }
+            __syncwarp();
+        }
     }
 }
 
