@@ -74,6 +74,11 @@ typedef enum {
 #define KC_CHECKSUM 0x4u     /* also compute the checksum in kclique_count */
 #define KC_NO_RULE1 0x8u     /* disable pruning Rule (1) (Sec. 4.3) */
 #define KC_ROWS_ONLY 0x10u   /* kclique_list: rows only; see kclique_list for the totals */
+#define KC_TRUSS_INNER 0x20u /* kclique_count: EBBkC-T (Alg. 3), every level of the branching in the
+                                global truss-based edge order instead of the colour order inside the
+                                sub-branches; no colouring, no Rules (1)-(2), no early termination (the
+                                ordering ablation of Sec. 6.2).  Not with kclique_list or per-edge outputs:
+                                KC_ERR_INVALID_ARG */
 
 typedef struct kc_graph kc_graph; /* opaque, device resident, immutable after prepare */
 
@@ -124,8 +129,8 @@ typedef struct {
 
 /*
  * kclique_prepare -- clean the graph and build the truss-based edge ordering and
- * the per-edge sub-branch vertex sets (paper Alg. 5 line 1; Sec. 4.2 Eq. 6;
- * Alg. 3 lines 2-4 VSet/ESet).
+ * the per-edge sub-branch vertex sets (paper Alg. 5; Sec. 4.2 Eq. 6;
+ * Alg. 3 VSet/ESet).
  *   row_ptr[n+1], col[nnz]: CSR of uint32; on_device != 0 means both are device
  *     pointers, else host pointers (copied in).  Caller keeps ownership.
  *   out: receives a new handle owned by the caller (free with kclique_release).
@@ -137,7 +142,7 @@ KC_API kc_status kclique_prepare(const uint32_t *row_ptr, const uint32_t *col, u
 
 /*
  * kclique_count -- exact number of k-cliques of a prepared graph (paper Alg. 5
- * lines 2-6 with EBBkC-C_Rec of Alg. 4, pruning Rules (1)-(2) of Sec. 4.3 and
+ * with EBBkC-C_Rec of Alg. 4, pruning Rules (1)-(2) of Sec. 4.3 and
  * early termination of Sec. 5).  p may be NULL (defaults).  r is written on
  * KC_OK.  k < 3 or k > KC_MAX_K: KC_ERR_INVALID_ARG.  k > tau + 2: count 0.
  */
@@ -162,7 +167,7 @@ KC_API kc_status kclique_list(const kc_graph *g, uint32_t k, uint32_t *d_out, ui
 /*
  * kclique_prepare_ordered -- kclique_prepare with a choice of the top-level edge order:
  *   KC_ORDER_TRUSS  the truss-based ordering (Sec. 4.2, Eq. 6): EBBkC-H, the default;
- *   KC_ORDER_COLOUR the colour-based ordering (Sec. 4.3, Alg. 4 lines 1-2): a greedy
+ *   KC_ORDER_COLOUR the colour-based ordering (Sec. 4.3, Alg. 4): a greedy
  *                   colouring of G in decreasing (degree, id) order, vertices sorted by
  *                   non-increasing colour (ties by id), each edge branching on the common
  *                   out-neighbours of its endpoints (EBBkC-C; the ablation of Sec. 6).
@@ -272,10 +277,16 @@ typedef struct {
     uint32_t max_batch;                /* count requests per batched call; 0 = 512 */
     uint32_t list_workers;             /* listings in flight at once; 0 = 4 */
     int32_t device;                    /* CUDA device of the GPU backend; -1 = the current one */
+    uint32_t upload_workers;           /* uploads prepared at once; 0 = 2 */
+    uint32_t yield_ms;                 /* short work first: a count batch waits while uploads or
+                                          listings are queued or running, at most this many
+                                          milliseconds; 0 = 100, KC_SERVER_NO_YIELD = never waits */
     uint32_t pad;
     kc_params params;                  /* for every count batch and listing (per-edge outputs must be NULL) */
     const kc_server_backend *backend;  /* NULL = the GPU */
 } kc_server_config;
+
+#define KC_SERVER_NO_YIELD 0xFFFFFFFFu
 
 #define KC_REQ_COUNT 0u
 #define KC_REQ_LIST 1u

@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libkclique.so")
 WIDTHS = (1, 2, 4, 8, 16, 32)
 SOURCES = (["kc_prepare.cu", "kc_branch.cu"] + [f"kc_branch_w{w}.cu" for w in WIDTHS] +
-           ["kc_api.cu", "kc_noalloc.cu", "kc_server.cu"])
+           ["kc_branch_t.cu", "kc_api.cu", "kc_noalloc.cu", "kc_server.cu"])
 HEADERS = ["kc_internal.cuh", "kc_branch_dev.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -72,6 +72,8 @@ kc_status run_one(const kc_graph *g, u32 k, const kc_params *p, cudaStream_t s, 
     memset(r, 0, sizeof(*r));
     if (k < 3 || k > KC_MAX_K) return KC_ERR_INVALID_ARG;
     if (list && cap && !d_out) return KC_ERR_INVALID_ARG;
+    const bool truss_inner = p && (p->flags & KC_TRUSS_INNER);
+    if (truss_inner && (list || p->d_edge_count || p->d_edge_checksum || p->d_edge_cycles)) return KC_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
     r->ms_prepare = g->ms_prepare;
     if (p && p->d_edge_count) KC_CUDA(cudaMemsetAsync(p->d_edge_count, 0, sizeof(u64) * (g->m ? g->m : 1), s));
@@ -111,7 +113,7 @@ kc_status run_one(const kc_graph *g, u32 k, const kc_params *p, cudaStream_t s, 
     // totals; once the buffer is full it stops, and the totals come from a count with
     // checksum instead (which may split heavy sub-branches; a listing pass cannot)
     cfg.stop_full = list;
-    st = kc_run_queries(&q, 1, &cfg, s, &acc, &ms, &msb);
+    st = truss_inner ? kc_run_ebbkc_t(g, k, &cfg, s, &acc, &ms, &msb) : kc_run_queries(&q, 1, &cfg, s, &acc, &ms, &msb);
     if (st != KC_OK) return st;
     st = map_device_status(acc.status);
     if (st != KC_OK) return st;

@@ -1,5 +1,5 @@
 // Branch engine, host side: the launches of the per-edge sub-branches of EBBkC-H
-// (paper Alg. 5 lines 2-6 with EBBkC-C_Rec of Alg. 4 and the early termination of
+// (paper Alg. 5 with EBBkC-C_Rec of Alg. 4 and the early termination of
 // Sec. 5).  The kernels are in kc_branch_dev.cuh, instantiated per bitset width in
 // kc_branch_w<W>.cu; this file builds the per-query descriptors, runs the width classes
 // and reads the results back, and holds the binomial table and the integer-peak probe.

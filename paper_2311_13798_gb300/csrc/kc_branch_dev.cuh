@@ -1,4 +1,4 @@
-// Branch engine, device side: the per-edge sub-branches of EBBkC-H (paper Alg. 5 lines 2-6,
+// Branch engine, device side: the per-edge sub-branches of EBBkC-H (paper Alg. 5,
 // EBBkC-C_Rec of Alg. 4) with early termination (Sec. 5), on one GB300.
 //
 // Work unit = one top-level edge e (a "ticket"), tickets sorted by |VSet(e)|
@@ -177,13 +177,6 @@ unsigned long long read_debug_flag() {
 #define KC_OK(i, n) true
 unsigned long long read_debug_flag() { return 0; }
 #endif
-__device__ __forceinline__ u64 zkey(u64 v) {
-    u64 x = v + 0x9E3779B97F4A7C15ull;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-    x = x ^ (x >> 31);
-    return x | 1ull;
-}
 
 __device__ __forceinline__ u128 add_sat(u128 a, u128 b) {
     u128 s = a + b;
@@ -1250,6 +1243,277 @@ __device__ void frame_l3_count(const Lay &L, const u32 *C, int lane, Acc &acc, i
     }
 }
 
+// ---------------------------------------------------------------- l = 4 frames
+// The 4-cliques of g[C] through its complement H (the missing pairs of C).  A 4-set of C
+// is a clique iff it spans no edge of H, so by inclusion-exclusion over the edge sets F
+// of H that span at most 4 vertices (sign (-1)^|F|, times the C(c-|V(F)|, 4-|V(F)|) ways
+// to complete V(F) to a 4-set):
+//   K4 = C(c,4) - M C(c-2,2) + (P3 - T)(c-3) + 2K2 - P4 - S3 + C4 + paw - diamond + K4(H)
+// over the subgraph types of H: M edges, P3 = sum_x C(dbar_x, 2) paths of two edges,
+// T triangles, 2K2 = C(M,2) - P3 pairs of disjoint edges, P4 = sum_{xa in H}
+// (dbar_x - 1)(dbar_a - 1) - 3T paths of three edges, S3 = sum_x C(dbar_x, 3) stars,
+// C4 = (1/2) sum_{x<y} C(codeg(x,y), 2) 4-cycles, paw = sum_x (dbar_x - 2) T_x (T_x
+// the triangles at x), diamond = sum_{xa in H} C(t_xa, 2) (t_xa the triangles on xa),
+// and the 4-cliques of H.
+// SUM: the checksum P * sum over 4-cliques of z_a z_b z_c z_d, by the same expansion
+// with every F weighted by the keys of V(F) times e_{4-|V(F)|} of the keys of C - V(F),
+// written without division (mod 2^64): with Z, e2, e4 the elementary symmetric sums of
+// C's keys, S1(x) and e_j(N(x)) those of x's H-neighbours, p_j their power sums, and
+// Q(x) = sum over H-edges ab inside N(x) of z_a z_b,
+//   e4 - sum_{xa in H} z_x z_a e2(C - {x, a}) + sum_x z_x ((Z - z_x) e2(N(x)) - (p1 p2 - p3))
+//   - Z T_z + sum_x z_x^2 Q(x) + [e2 over H-edges of z_x z_a - sum_x z_x^2 e2(N(x))]
+//   - P4_z - sum_x z_x e3(N(x)) + C4_z + sum_x (z_x S1(x) - 2 z_x^2) Q(x) - diamond_z + K4(H)_z
+// with T_z = sum over triangles of H of their key products, P4_z = sum_{xa in H} z_x z_a
+// ((S1(x) - z_a)(S1(a) - z_x) - sum_{b in N(x) & N(a)} z_b^2), C4_z = sum_{x<y} z_x z_y
+// e2(keys of N(x) & N(y) & {> x}) (each 4-cycle once, through its least vertex and the
+// one opposite), diamond_z = sum_{xa in H} z_x z_a e2(keys of N(x) & N(a)).
+// Lane per vertex x; its row of H is C & ~N(x) without x.  The cost is O(c^2 W) word
+// operations (the pairs of C4) plus work on the edges of H, against O(|E| c W) for
+// branching on the frame's edges, so it is taken only when H is sparse
+// (M <= E / KC_L4_DENSE); it returns false, and the frame branches, otherwise.
+#ifndef KC_L4  // count dense l = 4 frames whole (even k)
+#define KC_L4 1
+#endif
+#ifndef KC_L4_DENSE
+#define KC_L4_DENSE 3
+#endif
+
+__device__ __forceinline__ void poly4_mul(u64 &a1, u64 &a2, u64 &a3, u64 &a4, u64 b1, u64 b2, u64 b3, u64 b4) {
+    const u64 c4 = a4 + b4 + a1 * b3 + a2 * b2 + a3 * b1;
+    const u64 c3 = a3 + b3 + a1 * b2 + a2 * b1;
+    const u64 c2 = a2 + b2 + a1 * b1;
+    a1 += b1;
+    a2 = c2;
+    a3 = c3;
+    a4 = c4;
+}
+
+__device__ __forceinline__ void poly4_warp_product(u64 &p1, u64 &p2, u64 &p3, u64 &p4) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 b1 = __shfl_xor_sync(0xffffffffu, p1, o);
+        const u64 b2 = __shfl_xor_sync(0xffffffffu, p2, o);
+        const u64 b3 = __shfl_xor_sync(0xffffffffu, p3, o);
+        const u64 b4 = __shfl_xor_sync(0xffffffffu, p4, o);
+        poly4_mul(p1, p2, p3, p4, b1, b2, b3, b4);
+    }
+}
+
+// the H-row of vertex y in C: C & ~N(y) without y
+template <int W>
+__device__ __forceinline__ u32 hrow_word(const Lay &L, const u32 *cw, int y, int w) {
+    return cw[w] & ~L.A[y * (W + KC_ROW_PAD) + w] & ~((w == (y >> 5)) ? (1u << (y & 31)) : 0u);
+}
+
+template <int W, bool SUM>
+__device__ __noinline__ bool frame_l4_count(const Lay &L, const u32 *C, int lane, Acc &acc, int ws, u64 P) {
+    u32 cw[W];
+    int cnt = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        cw[w] = C[w];
+        cnt += __popc(cw[w]);
+    }
+    if (cnt < 4) return true;  // no 4-set
+    compact_positions<W>(cw, L.aux2, lane);
+    u64 sdb = 0;
+    u64 e1 = 0, e2 = 0, e3 = 0, e4 = 0;  // SUM: the lane's part of prod (1 + z x) over C
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        if (i < cnt) {
+            const int x = L.aux2[i];
+            int db = -1;  // x itself is not in N(x)
+#pragma unroll
+            for (int w = 0; w < W; w++) db += __popc(cw[w] & ~L.A[x * (W + KC_ROW_PAD) + w]);
+            L.aux[x] = (uint16_t)db;  // by vertex
+            sdb += (u64)db;
+            acc.ops += 2u * (u32)ws;
+            if (SUM) poly4_mul(e1, e2, e3, e4, L.z[x], 0ull, 0ull, 0ull);
+        }
+    }
+    sdb = warp_sum_u64(sdb);
+    const u64 c = (u64)cnt, M = sdb / 2, E = c * (c - 1) / 2 - M;
+    if (M * KC_L4_DENSE > E) return false;
+    if (SUM) poly4_warp_product(e1, e2, e3, e4);  // e1 = Z: every lane holds the sums over C
+    __syncwarp();
+    // The count's terms folded per element, each element of H visited once: a vertex x
+    // adds C(dbar_x, 2)(c - 4) - C(dbar_x, 3); an H-edge x < a adds -(dbar_x - 1)(dbar_a - 1)
+    // - C(t_xa, 2); a triangle x < a < b of H adds dbar_x + dbar_a + dbar_b - c (its parts of
+    // -T(c-3) + 3T + paw); a 4-cycle (counted at its least vertex x and the vertex y
+    // opposite) and a 4-clique of H add 1.  SUM: zs collects every weighted term but the
+    // e2 over H-edge weights, whose lane parts are ew1, ew2.
+    u64 kc = 0, zs = 0, ew1 = 0, ew2 = 0;
+    u32 words = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        if (i >= cnt) continue;
+        const int x = L.aux2[i];
+        const u64 dx = L.aux[x];
+        kc += dx * (dx - 1) / 2 * (c - 4) - dx * (dx - 1) * (dx - 2) / 6;
+        u32 hx[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) hx[w] = hrow_word<W>(L, cw, x, w);
+        const u64 zx = SUM ? L.z[x] : 0ull;
+        u64 s1 = 0, qx = 0;  // SUM: S1(x), Q(x)
+        if (SUM && dx) {
+            u64 q2 = 0, q3 = 0, n2 = 0, n3 = 0;
+#pragma unroll (W <= 8 ? W : 1)
+            for (int w = 0; w < W; w++) {
+                u32 nb = hx[w];
+                while (nb) {
+                    const u64 za = L.z[w * 32 + __ffs(nb) - 1];
+                    nb &= nb - 1;
+                    n3 += n2 * za;
+                    n2 += s1 * za;
+                    s1 += za;
+                    const u64 za2 = za * za;
+                    q2 += za2;
+                    q3 += za2 * za;
+                }
+            }
+            // paths of two edges, stars, pairs of H-edges that share x
+            zs += zx * ((e1 - zx) * n2 - (s1 * q2 - q3)) - zx * n3 - zx * zx * n2;
+        }
+        if (dx) {
+#pragma unroll (W <= 8 ? W : 1)
+            for (int w = 0; w < W; w++) {
+                u32 nb = hx[w];
+                while (nb) {
+                    const int a = w * 32 + __ffs(nb) - 1;
+                    nb &= nb - 1;
+                    if (!SUM && a < x) continue;
+                    u32 cm[W];  // common H-neighbours of x and a
+                    int t = 0;
+#pragma unroll
+                    for (int w2 = 0; w2 < W; w2++) {
+                        cm[w2] = hx[w2] & hrow_word<W>(L, cw, a, w2);
+                        t += __popc(cm[w2]);
+                    }
+                    words += (u32)W;
+                    u64 za = 0, zc_gt = 0, cz2 = 0, ce2 = 0;
+                    if (SUM) {
+                        za = L.z[a];
+                        u64 ce1 = 0;
+#pragma unroll (W <= 8 ? W : 1)
+                        for (int w2 = 0; w2 < W; w2++) {
+                            u32 bb = cm[w2];
+                            while (bb) {
+                                const int b = w2 * 32 + __ffs(bb) - 1;
+                                bb &= bb - 1;
+                                const u64 zb = L.z[b];
+                                if (b > a) zc_gt += zb;
+                                cz2 += zb * zb;
+                                ce2 += ce1 * zb;
+                                ce1 += zb;
+                            }
+                        }
+                        qx += za * zc_gt;
+                    }
+                    if (a < x) continue;
+                    const u64 da = L.aux[a];
+                    kc -= (dx - 1) * (da - 1) + (u64)t * (u64)(t - 1) / 2;
+                    if (SUM) {
+                        const u64 wt = zx * za;
+                        u64 s1a = 0;
+#pragma unroll (W <= 8 ? W : 1)
+                        for (int w2 = 0; w2 < W; w2++) {
+                            u32 bb = hrow_word<W>(L, cw, a, w2);
+                            while (bb) { s1a += L.z[w2 * 32 + __ffs(bb) - 1]; bb &= bb - 1; }
+                        }
+                        words += (u32)W;
+                        ew2 += ew1 * wt;
+                        ew1 += wt;
+                        // single edge (e2 of C - {x, a}), triangles on it above a, P4_z, diamond_z
+                        zs -= wt * (e2 - (zx + za) * (e1 - zx - za) - wt) + e1 * wt * zc_gt +
+                              wt * ((s1 - za) * (s1a - zx) - cz2) + wt * ce2;
+                    }
+                    // triangles x < a < b, and the 4-cliques of H whose least vertices are x < a
+#pragma unroll
+                    for (int w2 = 0; w2 < W; w2++) cm[w2] &= gt_mask(a, w2);
+                    if (t) {
+#pragma unroll (W <= 8 ? W : 1)
+                        for (int w2 = 0; w2 < W; w2++) {
+                            u32 bb = cm[w2];
+                            while (bb) {
+                                const int b = w2 * 32 + __ffs(bb) - 1;
+                                bb &= bb - 1;
+                                kc += dx + da + (u64)L.aux[b] - c;
+                                int q = 0;
+                                u64 zq = 0;
+#pragma unroll
+                                for (int w3 = 0; w3 < W; w3++) {
+                                    u32 qq = cm[w3] & ~L.A[b * (W + KC_ROW_PAD) + w3] & gt_mask(b, w3);
+                                    q += __popc(qq);
+                                    if (SUM) {
+                                        while (qq) { zq += L.z[w3 * 32 + __ffs(qq) - 1]; qq &= qq - 1; }
+                                    }
+                                }
+                                kc += (u64)q;
+                                if (SUM) zs += zx * za * L.z[b] * zq;
+                                words += (u32)W;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (SUM) zs += zx * qx * (s1 - zx);  // triangle and paw terms
+        // 4-cycles with least vertex x and opposite vertex y: common H-neighbours above x
+        if (dx >= 2) {
+            for (int j = i + 1; j < cnt; j++) {
+                const int y = L.aux2[j];
+                if (L.aux[y] < 2) continue;
+                // y is in hx & ~N(y) when xy is an H-edge (y is not its own neighbour): drop it
+                const u32 ybit = 1u << (y & 31);
+                const int yw = y >> 5;
+                u32 cn[W];
+                int cg = 0;
+#pragma unroll
+                for (int w = 0; w < W; w++) {
+                    cn[w] = hx[w] & ~L.A[y * (W + KC_ROW_PAD) + w] & gt_mask(x, w) & ~(w == yw ? ybit : 0u);
+                    cg += __popc(cn[w]);
+                }
+                kc += (u64)cg * (u64)(cg - 1) / 2;
+                words += (u32)W;
+                if (SUM && cg >= 2) {
+                    u64 f1 = 0, f2 = 0;  // e1, e2 of their keys
+#pragma unroll (W <= 8 ? W : 1)
+                    for (int w = 0; w < W; w++) {
+                        u32 bb = cn[w];
+                        while (bb) {
+                            const u64 zb = L.z[w * 32 + __ffs(bb) - 1];
+                            bb &= bb - 1;
+                            f2 += f1 * zb;
+                            f1 += zb;
+                        }
+                    }
+                    zs += zx * L.z[y] * f2;
+                }
+            }
+        }
+    }
+    acc.ops += 2u * words;
+    kc = warp_sum_u64(kc);
+    if (SUM) {
+        // e2 over all H-edge weights: the lanes' own e2 plus the products across lanes
+        u64 pre = ew1;
+        for (int o = 1; o < 32; o <<= 1) {
+            const u64 y = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += y;
+        }
+        pre -= ew1;  // key-weight sum of the lanes below
+        zs += ew2 + ew1 * pre;
+        zs = warp_sum_u64(zs);
+    }
+    if (lane == 0) {
+        const u64 cc4 = c * (c - 1) * (c - 2) * (c - 3) / 24;
+        const u64 cc2 = (c - 2) * (c - 3) / 2;
+        // unsigned arithmetic wraps consistently; the true value lies in [0, 2^64)
+        acc.leaf += cc4 - M * cc2 + M * (M - 1) / 2 + kc;
+        if (SUM) acc.csum += P * (e4 + zs);
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------- kernels
 // resident blocks per SM targeted by the register allocator, per bitset width
 template <int W>
@@ -1406,6 +1670,8 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                                                          LIST && !full);
             KC_SEC_END(2);
             if (closed) { phase = 3; continue; }
+            // even k, count and checksum modes: a dense l = 4 frame is counted whole through its complement
+            if (KC_L4 && EVEN && l == 4 && frame_l4_count<W, SUM>(L, C, lane, acc, Ws, P)) { phase = 3; continue; }
             if (lane == 0) { L.cur[d] = d == 0 ? u_lo - 1 : -1; L.rn[d] = 0; }
             if (lane < W) L.V[d * W + lane] = 0;
             __syncwarp();
@@ -1568,6 +1834,17 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                     u32 rest[W];  // cw without the positions visited so far (all <= xp)
 #pragma unroll
                     for (int w = 0; w < W; w++) rest[w] = cw[w];
+                    // SUM: zr = key sum over rest; a vertex's key sum over its neighbours in
+                    // rest is summed directly or, when its non-neighbours there are fewer
+                    // (dense frames), as zr minus the keys of those non-neighbours
+                    u64 zr = 0;
+                    if (SUM) {
+#pragma unroll (W <= 8 ? W : 1)
+                        for (int w = 0; w < W; w++) {
+                            u32 x = cw[w];
+                            while (x) { int b = __ffs(x) - 1; x &= x - 1; zr += L.z[w * 32 + b]; }
+                        }
+                    }
 #pragma unroll (W <= 8 ? W : 1)
                     for (int w = 0; w < W; w++) {
                         while (rest[w]) {
@@ -1575,17 +1852,31 @@ __device__ void run_dfs(const Lay &L, const Args &a, const QDesc &q, int s, int 
                             rest[w] &= rest[w] - 1;
                             const int xp = w * 32 + b;
                             acc.ops += 3u * (u32)(Ws - (xp >> 5));
-                            u64 zin = 0;
+                            int dn = 0, dm = 0;
 #pragma unroll
                             for (int w2 = 0; w2 < W; w2++) {
                                 if (w2 < w) continue;
-                                u32 y = L.A[xp * (W + KC_ROW_PAD) + w2] & rest[w2];
-                                ec += __popc(y);
-                                if (SUM) {
-                                    while (y) { int b2 = __ffs(y) - 1; y &= y - 1; zin += L.z[w2 * 32 + b2]; }
-                                }
+                                const u32 row = L.A[xp * (W + KC_ROW_PAD) + w2];
+                                dn += __popc(row & rest[w2]);
+                                if (SUM) dm += __popc(rest[w2] & ~row);
                             }
-                            if (SUM) zs += L.z[xp] * zin;
+                            ec += (u64)dn;
+                            if (SUM) {
+                                const u64 zx = L.z[xp];
+                                zr -= zx;
+                                const bool miss = dm < dn;
+                                u64 zin = 0;
+                                if (dn && dm) {
+#pragma unroll
+                                    for (int w2 = 0; w2 < W; w2++) {
+                                        if (w2 < w) continue;
+                                        const u32 row = L.A[xp * (W + KC_ROW_PAD) + w2];
+                                        u32 y = rest[w2] & (miss ? ~row : row);
+                                        while (y) { int b2 = __ffs(y) - 1; y &= y - 1; zin += L.z[w2 * 32 + b2]; }
+                                    }
+                                }
+                                zs += zx * (dm == 0 ? zr : miss ? zr - zin : zin);
+                            }
                         }
                     }
                     acc.leaf += ec;
@@ -1992,6 +2283,26 @@ branch_kernel(Args a) {
                 frame_l3_count<W, SUM>(L, L.C0, lane, acc, min((int)q.t_max, 2), use_et, Ws, P0);
                 KC_SEC_END(3);
             } else {
+                // even k: a top frame with l = 4 (k = 6) is tested and, when dense, counted
+                // whole in extraction order: neither the closed forms nor the l = 4 identity
+                // depend on the vertex order, so the colouring is done only for a frame that
+                // branches
+                const bool tested4 = KC_L4 && EVEN && l0 == 4;
+                if (tested4) {
+                    if (lane < W) L.C0[lane] = lt_mask(s, lane);
+                    __syncwarp();
+                    if (lane == 0) acc.nodes++;
+                    KC_SEC_BEGIN();
+                    const bool closed = early_terminate<W, MODE>(L, a, L.C0, 4, P0, lane, acc, use_et, Ws,
+                                                                 (uint16_t *)(L.childC + (size_t)32 * W),
+                                                                 (int)q.t_max, q, 0, false) ||
+                                        frame_l4_count<W, SUM>(L, L.C0, lane, acc, Ws, P0);
+                    KC_SEC_END(2);
+                    if (closed) {
+                        finish_unit<MODE>(q, e, acc, wt, lane, t_start);
+                        continue;
+                    }
+                }
                 KC_SEC_BEGIN();
                 const int ncol_ok = colour_and_order<W>(L, s, lane);
                 KC_SEC_END(1);
@@ -2043,7 +2354,7 @@ branch_kernel(Args a) {
                         // else: no room left, run the sub-branch here (below)
                     }
                 }
-                if (!done) run_dfs<W, MODE>(L, a, q, s, l0, P0, lane, acc, Ws, 0, s, !heavy, prof);
+                if (!done) run_dfs<W, MODE>(L, a, q, s, l0, P0, lane, acc, Ws, 0, s, !heavy && !tested4, prof);
             }
         }
         finish_unit<MODE>(q, e, acc, wt, lane, t_start);

@@ -31,6 +31,15 @@ void kc_note_launch();
 #define KC_DEV_ERR_TIMEOUT 0x8u
 #define KC_DEV_ERR_GRAPH 0x10u
 
+// The checksum's key of vertex v: the first output of SplitMix64 seeded with v, made odd.
+__device__ __forceinline__ u64 zkey(u64 v) {
+    u64 x = v + 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x = x ^ (x >> 31);
+    return x | 1ull;
+}
+
 // Device-resident prepared graph.
 struct kc_graph {
     int device;
@@ -111,6 +120,11 @@ struct kc_dev_acc {
 
 kc_status kc_run_queries(const kc_query *q, u32 nq, const kc_run_cfg *cfg, cudaStream_t s,
                          kc_dev_acc *h_acc, float *ms, float *ms_branch);
+
+// EBBkC-T (Alg. 3, kc_branch_t.cu): one count of g at k with every level of the branching
+// in the global truss-based edge order; cfg's flags (KC_CHECKSUM) and ticket shard apply
+kc_status kc_run_ebbkc_t(const kc_graph *g, u32 k, const kc_run_cfg *cfg, cudaStream_t s, kc_dev_acc *h_acc,
+                         float *ms, float *ms_branch);
 
 // early-termination threshold t of one query (0 = the paper's rule)
 u32 kc_pick_t(u32 t_max, u32 k, u32 tau);

@@ -1,4 +1,4 @@
-// Graph preparation on the device (paper Alg. 5 line 1 and Alg. 3 lines 2-4):
+// Graph preparation on the device (paper Alg. 5 and Alg. 3):
 //   A1  clean symmetric CSR (drop directions, duplicates, self-loops; Sec. 6.1)
 //   A2  edge ids, triangle listing on a degree orientation, per-edge triangle incidence
 //   A3  truss-based edge ordering (Sec. 4.2, Eq. 6) by level-synchronous peeling:
@@ -582,9 +582,20 @@ __device__ __forceinline__ void grid_sync(PeelState *ps) {
     __syncthreads();
 }
 
-#ifndef KC_PEEL_SOLO  // once at most this many edges remain, block 0 finishes the peel alone
-#define KC_PEEL_SOLO (1u << 15)  // (block barriers instead of grid barriers: the core's many
-#endif                           // small rounds are barrier-bound)
+// Block 0 finishes the peel alone (block barriers instead of grid barriers: a sparse
+// core's many small rounds are barrier-bound) once at most KC_PEEL_SOLO edges remain and
+// (remaining edges) x (least support + 1), a bound from below on the triangle work left,
+// is at most KC_PEEL_SOLO_WORK (a dense core's few big rounds need the whole grid).
+#ifndef KC_PEEL_SOLO
+#define KC_PEEL_SOLO (1u << 15)
+#endif
+#ifndef KC_PEEL_SOLO_WORK
+#define KC_PEEL_SOLO_WORK (1ull << 18)
+#endif
+
+#ifndef KC_PEEL_SMALL  // graphs with at most this many triangle incidences are peeled by one block
+#define KC_PEEL_SMALL (1ull << 18)
+#endif
 
 __device__ __forceinline__ u32 vld(const u32 *p) { return *(const volatile u32 *)p; }
 __device__ __forceinline__ uint8_t vld8(const uint8_t *p) { return *(const volatile uint8_t *)p; }
@@ -633,7 +644,7 @@ __global__ void __launch_bounds__(256) peel_persistent_kernel(u64 m, const u64 *
             if (nalive == 0) break;
             if (minsup > lvl) lvl = minsup;
             sync();  // all have read ctr[0..2]
-            if (!solo && nalive <= KC_PEEL_SOLO) {
+            if (!solo && nalive <= KC_PEEL_SOLO && nalive * (u64)(lvl + 1) <= KC_PEEL_SOLO_WORK) {
                 // every block took the same decision from the same nalive; the others leave
                 // and take no further part in any barrier
                 if (blockIdx.x != 0) return;
@@ -692,7 +703,7 @@ __global__ void __launch_bounds__(256) peel_persistent_kernel(u64 m, const u64 *
 }
 
 // ------------------------------------------------------------ colour-based ordering
-// EBBkC-C's top level (Sec. 4.3, Alg. 4 lines 1-2): a greedy colouring of G, vertices in
+// EBBkC-C's top level (Sec. 4.3, Alg. 4): a greedy colouring of G, vertices in
 // non-increasing colour (ties by id), each edge oriented to its later endpoint.  Greedy in
 // the order of decreasing (degree, id) is computed in rounds (Jones-Plassmann): a vertex
 // whose uncoloured neighbours all come later in that order takes the least colour none of
@@ -1016,16 +1027,33 @@ static kc_status prepare_body(const u32 *row_ptr_in, const u32 *col_in, u32 n, u
     KC_TRY(dalloc(&Fn, m, s, &scr));
     KC_TRY(dalloc(&ctr, 4, s, &scr));
     KC_CUDA(cudaMemsetAsync(st, 0, m ? m : 1, s));
-    u32 *h_ctr = nullptr;
-    KC_CUDA(cudaMallocHost(&h_ctr, sizeof(u32) * 4));
-    struct HostFree { u32 *p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{h_ctr};
+    // host copies of the counters: pageable (a pinned allocation per call would cost more
+    // than the few 4-byte reads, and freeing it waits for the whole device)
+    u32 h_ctr[4] = {0, 0, 0, 0};
     if (m) {
         iota_kernel<<<grid_for(m), TPB, 0, s>>>(alive, m);
         kc_note_launch();
     }
-    // one cooperative persistent launch when the device supports it (host-driven rounds otherwise)
+    // one cooperative persistent launch when the device supports it (host-driven rounds otherwise);
+    // a graph with few edges and triangles is peeled by one block from the start, in an ordinary launch
+    // that needs no co-resident grid, so it starts as soon as one SM has room
     bool peeled = false;
-    {
+    if (m > 0 && m <= KC_PEEL_SOLO && ninc <= KC_PEEL_SMALL) {
+        PeelState *ps;
+        KC_TRY(dalloc(&ps, 1, s, &scr));
+        KC_CUDA(cudaMemsetAsync(ps, 0, sizeof(PeelState), s));
+        peel_persistent_kernel<<<1, 256, 0, s>>>(m, inc_ptr, inc, sup, st, g->level, g->round, alive, alive2, F, Fn,
+                                                  ps);
+        kc_note_launch();
+        PeelState h;
+        KC_CUDA(cudaMemcpyAsync(&h, ps, sizeof(PeelState), cudaMemcpyDeviceToHost, s));
+        KC_CUDA(cudaStreamSynchronize(s));
+        if (h.status & KC_DEV_ERR_TIMEOUT) return KC_ERR_TIMEOUT;
+        if (h.status) return KC_ERR_CUDA;
+        g->rounds = h.rounds;
+        peeled = true;
+    }
+    if (!peeled) {
         int dev = 0, coop = 0, nsm = 0, per_sm = 0;
         KC_CUDA(cudaGetDevice(&dev));
         KC_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));

@@ -9,11 +9,15 @@
 //   * list workers (list_workers of them, each with its own CUDA stream and device row
 //     buffer) write the rows of listing requests with KC_ROWS_ONLY; a listing whose buffer
 //     filled gets its exact totals from a count entry that joins the next batch;
-//   * the upload worker prepares uploaded graphs on its own stream, after admitting them
-//     against the HBM budget (least-recently-used unpinned graphs that no request waits
-//     on are released to make room; an upload that still does not fit is rejected).
+//   * upload workers (upload_workers of them, each with its own stream) prepare uploaded
+//     graphs, after admitting them against the HBM budget (least-recently-used unpinned
+//     graphs that no request waits on are released to make room; an upload that still
+//     does not fit is rejected).
 // Counts, listings and prepares run on different streams, so their work overlaps on the
-// device.  Prepared graphs stay resident across requests.  There is no result cache.
+// device where the SMs have room.  A batch's persistent kernels fill every SM until its
+// slowest query ends, so short work goes first: while uploads or listings are queued or
+// running, the next batch waits for them (at most yield_ms).  Prepared graphs stay
+// resident across requests.  There is no result cache.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -38,17 +42,18 @@ double now_s() {
 // ------------------------------------------------------------------ the GPU backend
 struct GpuBackend {
     int device = 0;
-    cudaStream_t ustream = nullptr, qstream = nullptr;
+    cudaStream_t qstream = nullptr;
     kc_params params;
 };
 
-// per list-worker thread: a stream and a device row buffer, freed when the thread ends
-struct ListWorkerState {
+// per list- or upload-worker thread: a stream and a device row buffer, freed when the
+// thread ends
+struct WorkerState {
     int device = -1;
     cudaStream_t stream = nullptr;
     uint32_t *d_rows = nullptr;
     uint64_t bytes = 0;
-    ~ListWorkerState() {
+    ~WorkerState() {
         if (device >= 0) {
             cudaSetDevice(device);
             if (d_rows) cudaFree(d_rows);
@@ -56,14 +61,28 @@ struct ListWorkerState {
         }
     }
 };
-thread_local ListWorkerState t_list;
+thread_local WorkerState t_worker;
+
+// the calling worker thread's stream, created on first use
+kc_status worker_stream(const GpuBackend *b, cudaStream_t *s) {
+    WorkerState &w = t_worker;
+    if (w.device < 0) {
+        KC_CUDA(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
+        w.device = b->device;
+    }
+    *s = w.stream;
+    return KC_OK;
+}
 
 kc_status gpu_prepare(void *ctx, const uint32_t *row_ptr, const uint32_t *col, uint32_t n, uint64_t nnz,
                       void **graph, uint64_t *bytes) {
     GpuBackend *b = (GpuBackend *)ctx;
     KC_CUDA(cudaSetDevice(b->device));
+    cudaStream_t s;
+    kc_status st = worker_stream(b, &s);
+    if (st != KC_OK) return st;
     kc_graph *g = nullptr;
-    kc_status st = kclique_prepare(row_ptr, col, n, nnz, 0, (kc_stream)b->ustream, &g);
+    st = kclique_prepare(row_ptr, col, n, nnz, 0, (kc_stream)s, &g);
     if (st != KC_OK) return st;
     *graph = g;
     *bytes = g->resident_bytes;
@@ -83,11 +102,10 @@ kc_status gpu_count_batch(void *ctx, void *const *graphs, const uint32_t *ks, co
 kc_status gpu_list(void *ctx, void *graph, uint32_t k, uint32_t *rows, uint64_t cap, kc_result *r) {
     GpuBackend *b = (GpuBackend *)ctx;
     KC_CUDA(cudaSetDevice(b->device));
-    ListWorkerState &w = t_list;
-    if (w.device < 0) {
-        w.device = b->device;
-        KC_CUDA(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
-    }
+    cudaStream_t s;
+    kc_status st0 = worker_stream(b, &s);
+    if (st0 != KC_OK) return st0;
+    WorkerState &w = t_worker;
     const uint64_t need = sizeof(uint32_t) * (uint64_t)k * (cap ? cap : 1);
     if (need > w.bytes) {
         if (w.d_rows) KC_CUDA(cudaFree(w.d_rows));
@@ -151,6 +169,7 @@ struct kc_server {
     uint64_t next_ticket = 1, next_graph = 1, lru_clock = 0;
     uint64_t reserved = 0;            // estimated bytes of uploads being prepared
     uint64_t inflight = 0;            // submitted, not yet completed
+    uint32_t short_running = 0;       // uploads and listings on the GPU now
     bool stop = false;
     kc_server_counters st;
     std::vector<std::thread> threads;
@@ -251,12 +270,14 @@ void upload_worker(kc_server *sv) {
             continue;
         }
         sv->reserved += need;
+        sv->short_running++;
         lk.unlock();
         const double t0 = now_s();
         void *h = nullptr;
         uint64_t bytes = 0;
         kc_status st = sv->be.prepare(sv->be.ctx, q->rp.data(), q->col.data(), q->r.n, q->r.nnz, &h, &bytes);
         lk.lock();
+        sv->short_running--;
         sv->st.busy_upload_s += now_s() - t0;
         sv->reserved -= need;
         Graph &g = sv->graphs[gid];
@@ -286,6 +307,13 @@ void query_worker(kc_server *sv) {
     while (true) {
         sv->cv.wait(lk, [&] { return !sv->countq.empty() || (sv->stop && sv->inflight == 0); });
         if (sv->countq.empty()) return;
+        if (sv->cfg.yield_ms != KC_SERVER_NO_YIELD) {
+            // short work first (uploads, listings): for a while, they take the SMs first
+            const auto until = std::chrono::steady_clock::now() + std::chrono::milliseconds(sv->cfg.yield_ms);
+            sv->cv.wait_until(lk, until, [&] {
+                return sv->short_running == 0 && sv->uploadq.empty() && sv->listq.empty();
+            });
+        }
         batch.clear();
         hs.clear();
         ks.clear();
@@ -333,12 +361,14 @@ void list_worker(kc_server *sv) {
         Graph &g = sv->graphs[q->r.graph];
         g.lru = ++sv->lru_clock;
         void *h = g.h;
+        sv->short_running++;
         lk.unlock();
         kc_result r;
         memset(&r, 0, sizeof(r));
         const double t0 = now_s();
         kc_status st = sv->be.list(sv->be.ctx, h, q->r.k, q->r.rows, q->r.cap, &r);
         lk.lock();
+        sv->short_running--;
         sv->st.busy_list_s += now_s() - t0;
         if (st == KC_TRUNCATED && r.written >= q->r.cap) {
             // the buffer filled before the pass ended: the exact totals come from a count
@@ -370,6 +400,8 @@ kc_status kc_server_create(const kc_server_config *cfg, kc_server **out) {
     if (!sv->cfg.hbm_budget_bytes) sv->cfg.hbm_budget_bytes = 120ull << 30;
     if (!sv->cfg.max_batch) sv->cfg.max_batch = 512;
     if (!sv->cfg.list_workers) sv->cfg.list_workers = 4;
+    if (!sv->cfg.upload_workers) sv->cfg.upload_workers = 2;
+    if (!sv->cfg.yield_ms) sv->cfg.yield_ms = 100;
     if (sv->cfg.params.d_edge_count || sv->cfg.params.d_edge_checksum || sv->cfg.params.d_edge_cycles) {
         delete sv;
         return KC_ERR_INVALID_ARG;
@@ -394,11 +426,9 @@ kc_status kc_server_create(const kc_server_config *cfg, kc_server **out) {
         sv->gpu.device = dev;
         sv->gpu.params = sv->cfg.params;
         cudaError_t e = cudaSetDevice(dev);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->gpu.ustream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->gpu.qstream, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             kc_set_last_cuda_error(e, "kc_server_create streams", __FILE__, __LINE__);
-            if (sv->gpu.ustream) cudaStreamDestroy(sv->gpu.ustream);
             delete sv;
             return KC_ERR_CUDA;
         }
@@ -409,7 +439,7 @@ kc_status kc_server_create(const kc_server_config *cfg, kc_server **out) {
         sv->be.list = gpu_list;
         sv->be.release = gpu_release;
     }
-    sv->threads.emplace_back(upload_worker, sv);
+    for (uint32_t i = 0; i < sv->cfg.upload_workers; i++) sv->threads.emplace_back(upload_worker, sv);
     sv->threads.emplace_back(query_worker, sv);
     for (uint32_t i = 0; i < sv->cfg.list_workers; i++) sv->threads.emplace_back(list_worker, sv);
     *out = sv;
@@ -513,7 +543,6 @@ void kc_server_destroy(kc_server *sv) {
         if (kv.second.h) sv->be.release(sv->be.ctx, kv.second.h);
     if (sv->own_gpu) {
         cudaSetDevice(sv->gpu.device);
-        cudaStreamDestroy(sv->gpu.ustream);
         cudaStreamDestroy(sv->gpu.qstream);
     }
     delete sv;

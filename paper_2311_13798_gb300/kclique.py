@@ -33,6 +33,7 @@ KC_NO_RULE2 = 0x2
 KC_CHECKSUM = 0x4
 KC_NO_RULE1 = 0x8
 KC_ROWS_ONLY = 0x10
+KC_TRUSS_INNER = 0x20
 KC_ORDER_TRUSS = 0
 KC_ORDER_COLOUR = 1
 
@@ -60,6 +61,7 @@ class KcInfo(C.Structure):
 KC_REQ_COUNT = 0
 KC_REQ_LIST = 1
 KC_REQ_UPLOAD = 2
+KC_SERVER_NO_YIELD = 0xFFFFFFFF
 
 _PREPARE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32, C.c_uint64,
                           C.POINTER(C.c_void_p), C.POINTER(C.c_uint64))
@@ -77,7 +79,8 @@ class KcServerBackend(C.Structure):
 
 class KcServerConfig(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_batch", C.c_uint32), ("list_workers", C.c_uint32),
-                ("device", C.c_int32), ("pad", C.c_uint32), ("params", KcParams),
+                ("device", C.c_int32), ("upload_workers", C.c_uint32), ("yield_ms", C.c_uint32),
+                ("pad", C.c_uint32), ("params", KcParams),
                 ("backend", C.POINTER(KcServerBackend))]
 
 

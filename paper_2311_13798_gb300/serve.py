@@ -123,12 +123,15 @@ class _CallbackBackend:
 
 class KCliqueServer:
     def __init__(self, backend=None, hbm_budget_bytes: int = 120 << 30, max_batch: int = 512,
-                 list_workers: int = 4, device: int = -1, split_min: int = 0, t_max: int = 0, flags: int = 0):
+                 list_workers: int = 4, device: int = -1, split_min: int = 0, t_max: int = 0, flags: int = 0,
+                 upload_workers: int = 0, yield_ms: int = 0):
         self.lib = K.library()
         cfg = K.KcServerConfig()
         cfg.hbm_budget_bytes = int(hbm_budget_bytes)
         cfg.max_batch = int(max_batch)
         cfg.list_workers = int(list_workers)
+        cfg.upload_workers = int(upload_workers)
+        cfg.yield_ms = int(yield_ms)
         cfg.device = int(device)
         cfg.params = K._params(t_max=t_max, flags=flags, split_min=split_min)
         self._cb = _CallbackBackend(backend) if backend is not None else None

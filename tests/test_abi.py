@@ -58,7 +58,7 @@ def test_server_structs_match_the_header():
     assert ctypes.sizeof(K.KcRequest) == 4 + 4 + 8 + 8 + 8 + 8 + 8 + 4 + 4 + 8 + 4 * 4
     assert ctypes.sizeof(K.KcCompletion) == 8 + 8 + 4 + 4 + 4 + 4 + 8 * 4 + 8 + 8
     assert ctypes.sizeof(K.KcServerBackend) == 5 * 8
-    assert ctypes.sizeof(K.KcServerConfig) == 8 + 4 + 4 + 4 + 4 + ctypes.sizeof(K.KcParams) + 8
+    assert ctypes.sizeof(K.KcServerConfig) == 8 + 4 + 4 + 4 + 4 + 4 + 4 + ctypes.sizeof(K.KcParams) + 8
 
 
 def test_server_rejects_bad_requests_without_gpu():
