@@ -277,7 +277,7 @@ typedef struct {
     uint32_t max_batch;                /* count requests per batched call; 0 = 512 */
     uint32_t list_workers;             /* listings in flight at once; 0 = 4 */
     int32_t device;                    /* CUDA device of the GPU backend; -1 = the current one */
-    uint32_t upload_workers;           /* uploads prepared at once; 0 = 2 */
+    uint32_t upload_workers;           /* uploads prepared at once; 0 = 4 */
     uint32_t yield_ms;                 /* short work first: a count batch waits while uploads or
                                           listings are queued or running, at most this many
                                           milliseconds; 0 = 100, KC_SERVER_NO_YIELD = never waits */

@@ -40,11 +40,17 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+# the sources of the branch kernels whose DRAM counters bench.py reads from profiles/
+BRANCH_SOURCES = ["kc_internal.cuh", "kc_branch_dev.cuh", "kc_branch.cu"] + [f"kc_branch_w{w}.cu" for w in WIDTHS]
+
+
 def kernel_rev() -> str:
-    """Short hash of the CUDA sources (identifies the kernels behind stored ncu counters)."""
+    """Short hash of the branch kernels' sources (identifies the kernels behind stored ncu
+    counters; preparation, the entry points, the server and the EBBkC-T ablation kernel
+    do not enter it)."""
     import hashlib
     h = hashlib.sha256()
-    for src in SOURCES + HEADERS:
+    for src in BRANCH_SOURCES:
         h.update(open(os.path.join(CSRC, src), "rb").read())
     return h.hexdigest()[:12]
 

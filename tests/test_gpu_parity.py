@@ -7,6 +7,8 @@ and the degenerate cases of the method: empty graphs, triangle-free graphs
 (tau = 0), k > tau + 2, complete graphs (ET on the whole sub-branch), exact
 2-plexes, t-plexes, duplicate / self-loop / one-directional input.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -418,3 +420,39 @@ def test_colour_based_ordering_matches_oracle(cache, name):
         got = K.kclique_list(hc, k, out)
         rows = sorted(map(tuple, out.cpu().numpy().astype(np.int64).tolist()))
         assert rows == sorted(map(tuple, O.list_cliques(cg, k).astype(np.int64).tolist()))
+
+
+@pytest.mark.parametrize("name", ["gnp60", "gnp120_dense", "k40", "turan", "two_plex", "t3plex", "chung_lu", "sbm",
+                                  "appendix_b", "kpp", "wide"])
+def test_truss_order_at_every_level_matches_oracle(cache, name):
+    """EBBkC-T (Alg. 3): every level of the branching in the global truss-based edge
+    order, a child's graph being V(g) & VSet(e) with the edges of g after e.  A different
+    partition of the cliques than EBBkC-H's; the same counts and checksums."""
+    g, cg, h = get(cache, name)
+    K = kc()
+    for k in range(3, min(KMAX.get(name, 6), 6) + 1):
+        want = O.count(cg, k)
+        got = K.kclique_count(h, k, flags=K.KC_CHECKSUM | K.KC_TRUSS_INNER)
+        assert (got["count"], got["checksum"]) == (want["count"], want["checksum"]), (name, k)
+        assert K.kclique_count(h, k, flags=K.KC_TRUSS_INNER)["count"] == want["count"], (name, k)
+
+
+def test_truss_order_at_every_level_wide_and_invalid():
+    """K300: sub-branches of up to 298 vertices (16 bitset words); C(300, k) cliques with
+    checksum e_k of the keys.  Listing and per-edge outputs are refused with this flag."""
+    K = kc()
+    h = prep(G.complete(300))
+    keys = [O.key(v) for v in range(300)]
+    for k in (3, 4):
+        e = [1] + [0] * k
+        for x in keys:
+            for j in range(k, 0, -1):
+                e[j] = (e[j] + e[j - 1] * x) & M64
+        got = K.kclique_count(h, k, flags=K.KC_CHECKSUM | K.KC_TRUSS_INNER)
+        assert (got["count"], got["checksum"]) == (math.comb(300, k), e[k]), k
+    out = torch.empty((16, 4), dtype=torch.int32, device="cuda")
+    with pytest.raises(K.KCliqueError):
+        K.kclique_list(h, 4, out, flags=K.KC_TRUSS_INNER)
+    per_edge = torch.empty(int(K.kclique_info(h)["m"]), dtype=torch.int64, device="cuda")
+    with pytest.raises(K.KCliqueError):
+        K.kclique_count(h, 4, flags=K.KC_TRUSS_INNER, edge_count=per_edge)
