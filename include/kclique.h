@@ -216,6 +216,26 @@ KC_API kc_status kclique_count_batch_tuned(const kc_graph *const *graphs, const 
                                            uint32_t nq, const kc_params *p, kc_stream s, kc_result *results);
 
 /*
+ * Batch plans -- a batch that is counted again and again (the same graphs, ks and
+ * parameters) as one CUDA graph: kclique_batch_plan_create builds the batch's launch
+ * groups and their device buffer, runs the batch once (which sizes every buffer), then
+ * captures the copy of the buffer image, the persistent launches and the copy of the
+ * results back as one graph.  kclique_batch_plan_run replays it on stream s, waits for it
+ * and writes results[0..nq) exactly as kclique_count_batch_tuned would (ms_count: the
+ * replay's time).  Arguments of create as for kclique_count_batch_tuned; the graphs must
+ * outlive the plan, and no per-edge outputs may be set in p.  The plan owns its device
+ * and pinned host buffers until kclique_batch_plan_release.  One run of a plan at a time
+ * (runs of different plans may overlap on different streams).  Errors: as for the batch;
+ * a failure inside the capture releases everything made so far and returns KC_ERR_CUDA.
+ * The batching layer of the serving/batching design (no counterpart in the paper).
+ */
+typedef struct kc_batch_plan kc_batch_plan;
+KC_API kc_status kclique_batch_plan_create(const kc_graph *const *graphs, const uint32_t *ks, const kc_params *qp,
+                                           uint32_t nq, const kc_params *p, kc_stream s, kc_batch_plan **out);
+KC_API kc_status kclique_batch_plan_run(kc_batch_plan *plan, kc_stream s, kc_result *results);
+KC_API void kclique_batch_plan_release(kc_batch_plan *plan);
+
+/*
  * kclique_count_batch_noalloc -- the batched count of kclique_count_batch for callers
  * that cannot allocate device memory when they count (a fixed pre-reserved pool, a
  * driver-thread callback, a process at its memory limit).  The paper has no
@@ -280,7 +300,7 @@ typedef struct {
     uint32_t upload_workers;           /* uploads prepared at once; 0 = 4 */
     uint32_t yield_ms;                 /* short work first: a count batch waits while uploads or
                                           listings are queued or running, at most this many
-                                          milliseconds; 0 = 100, KC_SERVER_NO_YIELD = never waits */
+                                          milliseconds; 0 = 1000, KC_SERVER_NO_YIELD = never waits */
     uint32_t pad;
     kc_params params;                  /* for every count batch and listing (per-edge outputs must be NULL) */
     const kc_server_backend *backend;  /* NULL = the GPU */

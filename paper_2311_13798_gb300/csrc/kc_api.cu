@@ -156,6 +156,69 @@ kc_status run_one(const kc_graph *g, u32 k, const kc_params *p, cudaStream_t s, 
     return KC_OK;
 }
 
+// The queries of a batch that can have cliques (k <= tau + 2) and their indices; the
+// others keep zero results.
+kc_status batch_queries(const kc_graph *const *graphs, const uint32_t *ks, const kc_params *qp, uint32_t nq,
+                        kc_result *results, std::vector<kc_query> &qv, std::vector<u32> &idx, int *dev) {
+    memset(results, 0, sizeof(kc_result) * nq);
+    for (u32 i = 0; i < nq; i++) {
+        if (!graphs[i] || ks[i] < 3 || ks[i] > KC_MAX_K) return KC_ERR_INVALID_ARG;
+        if (*dev < 0) *dev = graphs[i]->device;
+        if (graphs[i]->device != *dev) return KC_ERR_INVALID_ARG;
+        results[i].ms_prepare = graphs[i]->ms_prepare;
+        if ((u64)ks[i] > (u64)graphs[i]->tau + 2) continue;
+        kc_status st = check_width(graphs[i], ks[i]);
+        if (st != KC_OK) return st;
+        kc_query q;
+        q.g = graphs[i];
+        q.k = ks[i];
+        q.ticket_begin = 0;
+        q.ticket_end = 0;
+        if (qp) {
+            q.t_max = qp[i].t_max;
+            q.split_min = qp[i].split_min;
+            q.width_min = qp[i].width_min;
+        }
+        qv.push_back(q);
+        idx.push_back(i);
+    }
+    return KC_OK;
+}
+
+kc_run_cfg batch_cfg(const kc_params *p) {
+    kc_run_cfg cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.t_max = pick_t(p);
+    cfg.flags = p ? p->flags : 0u;
+    cfg.warps_per_block = p ? p->warps_per_block : 0u;
+    cfg.blocks = p ? p->blocks : 0u;
+    cfg.split_min = p ? p->split_min : 0u;
+    cfg.width_min = p ? p->width_min : 0u;
+    return cfg;
+}
+
+// the accumulators of the run queries into their results; the worst device status
+kc_status batch_results(const std::vector<kc_dev_acc> &acc, const std::vector<u32> &idx, u32 flags, float ms,
+                        float msb, kc_result *results) {
+    kc_status worst = KC_OK;
+    for (size_t j = 0; j < idx.size(); j++) {
+        kc_result &r = results[idx[j]];
+        kc_status sj = map_device_status(acc[j].status);
+        if (sj != KC_OK) worst = sj;
+        r.count_lo = acc[j].count_lo;
+        r.count_hi = acc[j].count_hi;
+        r.checksum = (flags & KC_CHECKSUM) ? acc[j].checksum : 0ull;
+        r.edge_branches = acc[j].branches;
+        r.nodes = acc[j].nodes;
+        r.et_hits = acc[j].et_hits;
+        r.word_ops = acc[j].word_ops;
+        r.pair_tests = acc[j].pair_tests;
+        r.ms_count = ms;
+        r.ms_branch = msb;
+    }
+    return worst;
+}
+
 }  // namespace
 
 extern "C" {
@@ -246,62 +309,81 @@ kc_status kclique_count_batch_tuned(const kc_graph *const *graphs, const uint32_
     if (!graphs || !ks || !results) return KC_ERR_INVALID_ARG;
     if (p && (p->d_edge_count || p->d_edge_checksum || p->d_edge_cycles)) return KC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)sv;
-    memset(results, 0, sizeof(kc_result) * nq);
     std::vector<kc_query> qv;
     std::vector<u32> idx;
     int dev = -1;
-    for (u32 i = 0; i < nq; i++) {
-        if (!graphs[i] || ks[i] < 3 || ks[i] > KC_MAX_K) return KC_ERR_INVALID_ARG;
-        if (dev < 0) dev = graphs[i]->device;
-        if (graphs[i]->device != dev) return KC_ERR_INVALID_ARG;
-        results[i].ms_prepare = graphs[i]->ms_prepare;
-        if ((u64)ks[i] > (u64)graphs[i]->tau + 2) continue;
-        kc_status st = check_width(graphs[i], ks[i]);
-        if (st != KC_OK) return st;
-        kc_query q;
-        q.g = graphs[i];
-        q.k = ks[i];
-        q.ticket_begin = 0;
-        q.ticket_end = 0;
-        if (qp) {
-            q.t_max = qp[i].t_max;
-            q.split_min = qp[i].split_min;
-            q.width_min = qp[i].width_min;
-        }
-        qv.push_back(q);
-        idx.push_back(i);
-    }
-    if (qv.empty()) return KC_OK;
+    kc_status st = batch_queries(graphs, ks, qp, nq, results, qv, idx, &dev);
+    if (st != KC_OK || qv.empty()) return st;
     DeviceGuard dg(dev);
-    kc_run_cfg cfg;
-    memset(&cfg, 0, sizeof(cfg));
-    cfg.t_max = pick_t(p);
-    cfg.flags = p ? p->flags : 0u;
-    cfg.warps_per_block = p ? p->warps_per_block : 0u;
-    cfg.blocks = p ? p->blocks : 0u;
-    cfg.split_min = p ? p->split_min : 0u;
-    cfg.width_min = p ? p->width_min : 0u;
+    const kc_run_cfg cfg = batch_cfg(p);
     std::vector<kc_dev_acc> acc(qv.size());
     float ms = 0.f, msb = 0.f;
-    kc_status st = kc_run_queries(qv.data(), (u32)qv.size(), &cfg, s, acc.data(), &ms, &msb);
+    st = kc_run_queries(qv.data(), (u32)qv.size(), &cfg, s, acc.data(), &ms, &msb);
     if (st != KC_OK) return st;
-    kc_status worst = KC_OK;
-    for (size_t j = 0; j < qv.size(); j++) {
-        kc_result &r = results[idx[j]];
-        kc_status sj = map_device_status(acc[j].status);
-        if (sj != KC_OK) worst = sj;
-        r.count_lo = acc[j].count_lo;
-        r.count_hi = acc[j].count_hi;
-        r.checksum = (cfg.flags & KC_CHECKSUM) ? acc[j].checksum : 0ull;
-        r.edge_branches = acc[j].branches;
-        r.nodes = acc[j].nodes;
-        r.et_hits = acc[j].et_hits;
-        r.word_ops = acc[j].word_ops;
-        r.pair_tests = acc[j].pair_tests;
-        r.ms_count = ms;
-        r.ms_branch = msb;
+    return batch_results(acc, idx, cfg.flags, ms, msb, results);
+}
+
+}  // extern "C"
+
+struct kc_batch_plan {
+    kc_plan *plan = nullptr;         // null when no query can have cliques
+    int device = 0;
+    u32 nq = 0;
+    u32 flags = 0;
+    std::vector<u32> idx;            // the run queries' indices
+    std::vector<float> ms_prepare;   // per query
+};
+
+extern "C" {
+
+kc_status kclique_batch_plan_create(const kc_graph *const *graphs, const uint32_t *ks, const kc_params *qp,
+                                    uint32_t nq, const kc_params *p, kc_stream sv, kc_batch_plan **out) {
+    if (!graphs || !ks || !out) return KC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (p && (p->d_edge_count || p->d_edge_checksum || p->d_edge_cycles)) return KC_ERR_INVALID_ARG;
+    std::vector<kc_result> res(nq ? nq : 1);
+    std::vector<kc_query> qv;
+    kc_batch_plan *bp = new kc_batch_plan();
+    int dev = -1;
+    kc_status st = batch_queries(graphs, ks, qp, nq, res.data(), qv, bp->idx, &dev);
+    if (st != KC_OK) {
+        delete bp;
+        return st;
     }
-    return worst;
+    bp->nq = nq;
+    bp->flags = p ? p->flags : 0u;
+    for (u32 i = 0; i < nq; i++) bp->ms_prepare.push_back(res[i].ms_prepare);
+    if (!qv.empty()) {
+        bp->device = dev;
+        DeviceGuard dg(dev);
+        const kc_run_cfg cfg = batch_cfg(p);
+        st = kc_plan_create(qv.data(), (u32)qv.size(), &cfg, (cudaStream_t)sv, &bp->plan);
+        if (st != KC_OK) {
+            delete bp;
+            return st;
+        }
+    }
+    *out = bp;
+    return KC_OK;
+}
+
+kc_status kclique_batch_plan_run(kc_batch_plan *bp, kc_stream sv, kc_result *results) {
+    if (!bp || !results) return KC_ERR_INVALID_ARG;
+    memset(results, 0, sizeof(kc_result) * bp->nq);
+    for (u32 i = 0; i < bp->nq; i++) results[i].ms_prepare = bp->ms_prepare[i];
+    if (!bp->plan) return KC_OK;
+    DeviceGuard dg(bp->device);
+    std::vector<kc_dev_acc> acc(bp->idx.size());
+    float ms = 0.f;
+    kc_status st = kc_plan_run(bp->plan, (cudaStream_t)sv, acc.data(), &ms);
+    if (st != KC_OK) return st;
+    return batch_results(acc, bp->idx, bp->flags, ms, ms, results);
+}
+
+void kclique_batch_plan_release(kc_batch_plan *bp) {
+    if (!bp) return;
+    kc_plan_free(bp->plan);
+    delete bp;
 }
 
 }  // extern "C"

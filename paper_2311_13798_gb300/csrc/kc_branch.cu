@@ -171,22 +171,16 @@ struct Group {
     std::vector<u64> qstart;
     u64 off_qs = 0, off_qstart = 0, off_ctr = 0;
 };
-}  // namespace
 
-// Run queries: the tickets of each query are split into width classes, and the queries
-// of one class and one parity of k form a launch group (the kernels are compiled per
-// parity).  Every group's descriptors, ticket prefix and counters are written to one
-// device buffer by one copy, so the groups launch back to back on the stream with no
-// host synchronisation between them; the host waits once, for the results.
-kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cudaStream_t s, kc_dev_acc *h_acc,
-                         float *ms, float *ms_branch) {
-    kc_status st = kc_ensure_tables(s);
-    if (st != KC_OK) return st;
-    int dev = 0;
-    KC_CUDA(cudaGetDevice(&dev));
+// The launch groups of a set of queries, and the layout of the device buffer they share.
+struct Batch {
+    std::vector<Group> groups;
+    u64 bytes = 0;
+};
+
+void plan_batch(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, Batch *bt) {
     const int base_mode = cfg->list ? (MODE_LIST | MODE_CHECKSUM) : ((cfg->flags & KC_CHECKSUM) ? MODE_CHECKSUM : 0);
     const int widths[6] = {32, 16, 8, 4, 2, 1};
-    std::vector<Group> groups;
     for (int wi = 0; wi < 6; wi++) {
         const int W = widths[wi];
         for (int par = 0; par < (cfg->list ? 1 : 2); par++) {
@@ -220,12 +214,12 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
             if (gr.qs.empty()) continue;
             gr.qstart.assign(gr.qs.size() + 1, 0);
             for (size_t i = 0; i < gr.qs.size(); i++) gr.qstart[i + 1] = gr.qstart[i] + gr.qs[i].nt;
-            groups.push_back(std::move(gr));
+            bt->groups.push_back(std::move(gr));
         }
     }
     // one device buffer: accumulators, then per group its descriptors, prefix and counters
     u64 bytes = align256(sizeof(kc_dev_acc) * (nq ? nq : 1));
-    for (Group &gr : groups) {
+    for (Group &gr : bt->groups) {
         gr.off_qs = bytes;
         bytes += align256(sizeof(QDesc) * gr.qs.size());
         gr.off_qstart = bytes;
@@ -233,16 +227,23 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
         gr.off_ctr = bytes;
         bytes += align256(4 * sizeof(unsigned long long));
     }
-    unsigned char *dbuf = nullptr;
-    KC_CUDA(cudaMallocAsync(&dbuf, bytes, s));
+    bt->bytes = bytes;
+}
+
+// The host image of the device buffer at dbuf: zeroed accumulators and counters, each
+// group's descriptors (accumulator pointers into dbuf) and ticket prefix.
+void batch_image(const Batch &bt, unsigned char *dbuf, unsigned char *host) {
+    memset(host, 0, bt.bytes);
     kc_dev_acc *d_acc = (kc_dev_acc *)dbuf;
-    std::vector<unsigned char> host(bytes, 0);  // zeroed accumulators and counters
-    for (Group &gr : groups) {
-        for (QDesc &d : gr.qs) d.acc = d_acc + (uintptr_t)d.acc;
-        memcpy(host.data() + gr.off_qs, gr.qs.data(), sizeof(QDesc) * gr.qs.size());
-        memcpy(host.data() + gr.off_qstart, gr.qstart.data(), sizeof(u64) * gr.qstart.size());
+    for (const Group &gr : bt.groups) {
+        std::vector<QDesc> qs = gr.qs;
+        for (QDesc &d : qs) d.acc = d_acc + (uintptr_t)d.acc;
+        memcpy(host + gr.off_qs, qs.data(), sizeof(QDesc) * qs.size());
+        memcpy(host + gr.off_qstart, gr.qstart.data(), sizeof(u64) * gr.qstart.size());
     }
-    SplitBufs sb;
+}
+
+Args batch_args(const kc_run_cfg *cfg, int dev) {
     Args a;
     memset(&a, 0, sizeof(a));
     a.t_max = cfg->t_max;
@@ -251,6 +252,47 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
     a.cap = cfg->cap;
     a.stop_full = cfg->list && cfg->stop_full ? 1u : 0u;
     a.binom = g_tables[dev];
+    return a;
+}
+
+// The groups' launches on s, back to back (ev: two events per group, or null).
+kc_status launch_batch(const Batch &bt, const Args &a, const kc_run_cfg *cfg, cudaStream_t s, unsigned char *dbuf,
+                       SplitBufs *sb, cudaEvent_t *ev) {
+    kc_status st = KC_OK;
+    for (size_t gi = 0; gi < bt.groups.size() && st == KC_OK; gi++) {
+        const Group &gr = bt.groups[gi];
+        if (ev) KC_CUDA(cudaEventRecord(ev[2 * gi], s));
+        st = launch_width(gr.W, gr.mode, a, gr.qs, gr.qstart.back(), cfg, s, (QDesc *)(dbuf + gr.off_qs),
+                          (u64 *)(dbuf + gr.off_qstart), (unsigned long long *)(dbuf + gr.off_ctr), sb);
+        if (ev) KC_CUDA(cudaEventRecord(ev[2 * gi + 1], s));
+    }
+    return st;
+}
+
+}  // namespace
+
+// Run queries: the tickets of each query are split into width classes, and the queries
+// of one class and one parity of k form a launch group (the kernels are compiled per
+// parity).  Every group's descriptors, ticket prefix and counters are written to one
+// device buffer by one copy, so the groups launch back to back on the stream with no
+// host synchronisation between them; the host waits once, for the results.
+kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cudaStream_t s, kc_dev_acc *h_acc,
+                         float *ms, float *ms_branch) {
+    kc_status st = kc_ensure_tables(s);
+    if (st != KC_OK) return st;
+    int dev = 0;
+    KC_CUDA(cudaGetDevice(&dev));
+    Batch bt;
+    plan_batch(qv, nq, cfg, &bt);
+    std::vector<Group> &groups = bt.groups;
+    const u64 bytes = bt.bytes;
+    unsigned char *dbuf = nullptr;
+    KC_CUDA(cudaMallocAsync(&dbuf, bytes, s));
+    kc_dev_acc *d_acc = (kc_dev_acc *)dbuf;
+    std::vector<unsigned char> host(bytes);
+    batch_image(bt, dbuf, host.data());
+    SplitBufs sb;
+    Args a = batch_args(cfg, dev);
     a.prof = (KC_SECTION_PROFILE && getenv("KC_PROFILE")) ? 1u : 0u;
     if (a.prof) {
         KC_CUDA(cudaMallocAsync(&a.l3hist, 64 * sizeof(unsigned long long), s));
@@ -269,13 +311,7 @@ kc_status kc_run_queries(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cuda
     if (cfg->d_edge_cycles)
         KC_CUDA(cudaMemsetAsync(cfg->d_edge_cycles, 0, sizeof(u64) * (nq ? qv[0].g->m : 0), s));
     const bool profile = getenv("KC_PROFILE") != nullptr;
-    for (size_t gi = 0; gi < groups.size() && st == KC_OK; gi++) {
-        Group &gr = groups[gi];
-        KC_CUDA(cudaEventRecord(ev[2 + 2 * gi], s));
-        st = launch_width(gr.W, gr.mode, a, gr.qs, gr.qstart.back(), cfg, s, (QDesc *)(dbuf + gr.off_qs),
-                          (u64 *)(dbuf + gr.off_qstart), (unsigned long long *)(dbuf + gr.off_ctr), &sb);
-        KC_CUDA(cudaEventRecord(ev[3 + 2 * gi], s));
-    }
+    st = launch_batch(bt, a, cfg, s, dbuf, &sb, ev.data() + 2);
     KC_CUDA(cudaEventRecord(ev[1], s));
     if (st == KC_OK) KC_CUDA(cudaMemcpyAsync(h_acc, d_acc, sizeof(kc_dev_acc) * nq, cudaMemcpyDeviceToHost, s));
     cudaStreamSynchronize(s);
@@ -474,3 +510,122 @@ kc_status kc_run_queries_in_scratch(const kc_query *qv, u32 nq, const kc_run_cfg
     return KC_OK;
 }
 
+
+// ---------------------------------------------------------------- batch plans
+// One batch's work captured once as a CUDA graph: the copy of the buffer image (which
+// also zeroes the accumulators and counters), the launch groups and the copy of the
+// results back to pinned host memory.  A run replays it.
+struct kc_plan {
+    int device = 0;
+    u32 nq = 0;
+    u32 launches = 0;                          // kernel launches per run
+    kc_run_cfg cfg;
+    Batch bt;
+    unsigned char *dbuf = nullptr;             // device buffer
+    unsigned char *hbuf = nullptr;             // its pinned host image
+    kc_dev_acc *h_acc = nullptr;               // pinned copy of the accumulators
+    SplitBufs sb;
+    cudaStream_t cs = nullptr;                 // the stream the graph was captured on
+    cudaGraphExec_t exec = nullptr;
+};
+
+void kc_plan_free(kc_plan *p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->cs) {
+        if (p->sb.slots) cudaFreeAsync(p->sb.slots, p->cs);
+        cudaStreamSynchronize(p->cs);
+        cudaStreamDestroy(p->cs);
+    }
+    if (p->dbuf) cudaFree(p->dbuf);
+    if (p->hbuf) cudaFreeHost(p->hbuf);
+    if (p->h_acc) cudaFreeHost(p->h_acc);
+    delete p;
+}
+
+kc_status kc_plan_create(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cudaStream_t s, kc_plan **out) {
+    *out = nullptr;
+    if (cfg->list || cfg->d_edge_count || cfg->d_edge_checksum || cfg->d_edge_cycles) return KC_ERR_INVALID_ARG;
+    kc_status st = kc_ensure_tables(s);
+    if (st != KC_OK) return st;
+    kc_plan *p = new kc_plan();
+    auto fail = [&](kc_status e) { kc_plan_free(p); return e; };
+    auto cuda = [&](cudaError_t e, const char *what) {
+        if (e == cudaSuccess) return KC_OK;
+        kc_set_last_cuda_error(e, what, __FILE__, __LINE__);
+        return e == cudaErrorMemoryAllocation ? KC_ERR_OOM : KC_ERR_CUDA;
+    };
+    if ((st = cuda(cudaGetDevice(&p->device), "cudaGetDevice")) != KC_OK) return fail(st);
+    p->nq = nq;
+    p->cfg = *cfg;
+    plan_batch(qv, nq, cfg, &p->bt);
+    if ((st = cuda(cudaMalloc(&p->dbuf, p->bt.bytes), "cudaMalloc")) != KC_OK) return fail(st);
+    if ((st = cuda(cudaMallocHost(&p->hbuf, p->bt.bytes), "cudaMallocHost")) != KC_OK) return fail(st);
+    if ((st = cuda(cudaMallocHost(&p->h_acc, sizeof(kc_dev_acc) * (nq ? nq : 1)), "cudaMallocHost")) != KC_OK)
+        return fail(st);
+    batch_image(p->bt, p->dbuf, p->hbuf);
+    if ((st = cuda(cudaStreamCreateWithFlags(&p->cs, cudaStreamNonBlocking), "cudaStreamCreate")) != KC_OK)
+        return fail(st);
+    // the caller's stream's earlier work (the graphs' preparation) comes first
+    cudaEvent_t dep;
+    if ((st = cuda(cudaEventCreateWithFlags(&dep, cudaEventDisableTiming), "cudaEventCreate")) != KC_OK) return fail(st);
+    cudaEventRecord(dep, s);
+    cudaStreamWaitEvent(p->cs, dep, 0);
+    cudaEventDestroy(dep);
+    const Args a = batch_args(cfg, p->device);
+    // an ordinary first run sizes the buffers of split sub-branches, so the captured
+    // launches allocate nothing
+    if ((st = cuda(cudaMemcpyAsync(p->dbuf, p->hbuf, p->bt.bytes, cudaMemcpyHostToDevice, p->cs), "cudaMemcpyAsync")) !=
+        KC_OK)
+        return fail(st);
+    if ((st = launch_batch(p->bt, a, cfg, p->cs, p->dbuf, &p->sb, nullptr)) != KC_OK) return fail(st);
+    if ((st = cuda(cudaStreamSynchronize(p->cs), "first run")) != KC_OK) return fail(st);
+    // capture (relaxed: the launch code queries occupancy and sets kernel attributes)
+    const unsigned long long n0 = kclique_launch_count(0);
+    if ((st = cuda(cudaStreamBeginCapture(p->cs, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture")) != KC_OK)
+        return fail(st);
+    cudaError_t ce = cudaMemcpyAsync(p->dbuf, p->hbuf, p->bt.bytes, cudaMemcpyHostToDevice, p->cs);
+    kc_status lst = ce == cudaSuccess ? launch_batch(p->bt, a, cfg, p->cs, p->dbuf, &p->sb, nullptr) : KC_ERR_CUDA;
+    if (ce == cudaSuccess && lst == KC_OK)
+        ce = cudaMemcpyAsync(p->h_acc, p->dbuf, sizeof(kc_dev_acc) * nq, cudaMemcpyDeviceToHost, p->cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(p->cs, &graph);  // always ends the capture
+    p->launches = (u32)(kclique_launch_count(0) - n0);
+    if (lst != KC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(lst);
+    }
+    if ((st = cuda(ce != cudaSuccess ? ce : ee, "stream capture")) != KC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(st);
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&p->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if ((st = cuda(ie, "cudaGraphInstantiate")) != KC_OK) return fail(st);
+    *out = p;
+    return KC_OK;
+}
+
+kc_status kc_plan_run(kc_plan *p, cudaStream_t s, kc_dev_acc *h_acc, float *ms) {
+    int cur = 0;
+    KC_CUDA(cudaGetDevice(&cur));
+    if (cur != p->device) KC_CUDA(cudaSetDevice(p->device));
+    cudaEvent_t ev[2];
+    KC_CUDA(cudaEventCreate(&ev[0]));
+    KC_CUDA(cudaEventCreate(&ev[1]));
+    KC_CUDA(cudaEventRecord(ev[0], s));
+    const cudaError_t le = cudaGraphLaunch(p->exec, s);
+    KC_CUDA(cudaEventRecord(ev[1], s));
+    const cudaError_t se = cudaStreamSynchronize(s);
+    *ms = 0.f;
+    cudaEventElapsedTime(ms, ev[0], ev[1]);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (cur != p->device) cudaSetDevice(cur);
+    KC_CUDA(le);
+    KC_CUDA(se);
+    for (u32 i = 0; i < p->launches; i++) kc_note_launch();
+    memcpy(h_acc, p->h_acc, sizeof(kc_dev_acc) * p->nq);
+    return KC_OK;
+}

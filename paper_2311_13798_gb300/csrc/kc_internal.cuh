@@ -121,6 +121,13 @@ struct kc_dev_acc {
 kc_status kc_run_queries(const kc_query *q, u32 nq, const kc_run_cfg *cfg, cudaStream_t s,
                          kc_dev_acc *h_acc, float *ms, float *ms_branch);
 
+// Batch plans (kc_branch.cu): the launches of one batch of queries captured once as a
+// CUDA graph and replayed per run (one run of a plan at a time)
+struct kc_plan;
+kc_status kc_plan_create(const kc_query *qv, u32 nq, const kc_run_cfg *cfg, cudaStream_t s, kc_plan **out);
+kc_status kc_plan_run(kc_plan *p, cudaStream_t s, kc_dev_acc *h_acc, float *ms);
+void kc_plan_free(kc_plan *p);
+
 // EBBkC-T (Alg. 3, kc_branch_t.cu): one count of g at k with every level of the branching
 // in the global truss-based edge order; cfg's flags (KC_CHECKSUM) and ticket shard apply
 kc_status kc_run_ebbkc_t(const kc_graph *g, u32 k, const kc_run_cfg *cfg, cudaStream_t s, kc_dev_acc *h_acc,

@@ -401,7 +401,7 @@ kc_status kc_server_create(const kc_server_config *cfg, kc_server **out) {
     if (!sv->cfg.max_batch) sv->cfg.max_batch = 512;
     if (!sv->cfg.list_workers) sv->cfg.list_workers = 4;
     if (!sv->cfg.upload_workers) sv->cfg.upload_workers = 4;
-    if (!sv->cfg.yield_ms) sv->cfg.yield_ms = 100;
+    if (!sv->cfg.yield_ms) sv->cfg.yield_ms = 1000;
     if (sv->cfg.params.d_edge_count || sv->cfg.params.d_edge_checksum || sv->cfg.params.d_edge_cycles) {
         delete sv;
         return KC_ERR_INVALID_ARG;

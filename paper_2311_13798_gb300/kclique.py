@@ -175,6 +175,13 @@ def _load():
             lib.kclique_count_batch.restype = C.c_int
             lib.kclique_count_batch.argtypes = [C.POINTER(vp), C.POINTER(u32), u32, C.POINTER(KcParams), vp,
                                                 C.POINTER(KcResult)]
+            lib.kclique_batch_plan_create.restype = C.c_int
+            lib.kclique_batch_plan_create.argtypes = [C.POINTER(vp), C.POINTER(u32), C.POINTER(KcParams), u32,
+                                                      C.POINTER(KcParams), vp, C.POINTER(vp)]
+            lib.kclique_batch_plan_run.restype = C.c_int
+            lib.kclique_batch_plan_run.argtypes = [vp, vp, C.POINTER(KcResult)]
+            lib.kclique_batch_plan_release.restype = None
+            lib.kclique_batch_plan_release.argtypes = [vp]
             _lib = lib
     return _lib
 
@@ -344,6 +351,54 @@ def kclique_count_batch(graphs: list[Graph], ks, stream=None, tuner=None, choice
     if st != KC_OK:
         raise KCliqueError(st, "kclique_count_batch")
     return [_result(res[i], KC_OK) for i in range(nq)]
+
+
+class BatchPlan:
+    """A batch of count queries captured once as a CUDA graph and replayed by ``run``
+    (kclique_batch_plan_*).  The graphs must stay alive while the plan is used."""
+
+    def __init__(self, handle, nq: int, graphs):
+        self.handle, self.nq, self._graphs = handle, nq, graphs
+
+    def run(self, stream=None) -> list[dict]:
+        res = (KcResult * max(self.nq, 1))()
+        st = _load().kclique_batch_plan_run(self.handle, _stream(stream), res)
+        if st != KC_OK:
+            raise KCliqueError(st, "kclique_batch_plan_run")
+        return [_result(res[i], KC_OK) for i in range(self.nq)]
+
+    def release(self):
+        if self.handle:
+            _load().kclique_batch_plan_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def kclique_batch_plan_create(graphs: list[Graph], ks, choices=None, stream=None, **kw) -> BatchPlan:
+    """Capture the batch (graphs, ks), with optional per-query ``choices``, for replays."""
+    nq = len(graphs)
+    hs = (C.c_void_p * max(nq, 1))(*[g.handle for g in graphs])
+    kk = (C.c_uint32 * max(nq, 1))(*[int(k) for k in ks])
+    p = _params(**kw)
+    qp = (KcParams * max(nq, 1))(*[_params(**c) for c in choices]) if choices is not None else None
+    h = C.c_void_p()
+    st = _load().kclique_batch_plan_create(hs, kk, qp, nq, C.byref(p), _stream(stream), C.byref(h))
+    if st != KC_OK:
+        raise KCliqueError(st, "kclique_batch_plan_create")
+    return BatchPlan(h.value, nq, list(graphs))
+
+
+def kclique_batch_plan_run(plan: BatchPlan, stream=None) -> list[dict]:
+    return plan.run(stream)
+
+
+def kclique_batch_plan_release(plan: BatchPlan) -> None:
+    plan.release()
 
 
 def kclique_count_batch_tuned(graphs: list[Graph], ks, choices, stream=None, **kw) -> list[dict]:

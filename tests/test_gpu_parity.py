@@ -456,3 +456,30 @@ def test_truss_order_at_every_level_wide_and_invalid():
     per_edge = torch.empty(int(K.kclique_info(h)["m"]), dtype=torch.int64, device="cuda")
     with pytest.raises(K.KCliqueError):
         K.kclique_count(h, 4, flags=K.KC_TRUSS_INNER, edge_count=per_edge)
+
+
+def test_batch_plan_replays_match_oracle(cache):
+    """A batch captured once as a CUDA graph (kclique_batch_plan_*) and replayed: every
+    replay gives the oracle's counts and checksums, also with split sub-branches (the
+    item kernel inside the graph) and with a query that has no k-clique (k > tau + 2)."""
+    K = kc()
+    hs, ks, wants, choices = [], [], [], []
+    for name in ("gnp60", "k40", "two_plex", "chung_lu", "sbm", "wide", "kpp"):
+        g, cg, h = get(cache, name)
+        for k in (4, 5, 7):
+            if k > KMAX.get(name, 9):
+                continue
+            want = O.count(cg, k)
+            hs.append(h)
+            ks.append(k)
+            wants.append((want["count"], want["checksum"]))
+            choices.append({"split_min": 3} if k >= 7 else {})
+    plan = K.kclique_batch_plan_create(hs, ks, choices=choices, flags=K.KC_CHECKSUM)
+    try:
+        for _ in range(3):
+            got = plan.run()
+            assert [(r["count"], r["checksum"]) for r in got] == wants
+    finally:
+        plan.release()
+    once = K.kclique_count_batch(hs, ks, choices=choices, flags=K.KC_CHECKSUM)
+    assert [(r["count"], r["checksum"]) for r in once] == wants
