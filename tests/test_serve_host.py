@@ -151,3 +151,49 @@ def test_invalid_requests():
     with pytest.raises(K.KCliqueError):
         srv.submit(_req("count", "g", k=2))
     srv.close()
+
+
+class RecordingBackend(FakeBackend):
+    """FakeBackend that logs when prepares and count batches start and end."""
+
+    def __init__(self, prepare_delay):
+        super().__init__(delay=0.0)
+        self.prepare_delay = prepare_delay
+        self.log = []
+
+    def prepare(self, rp, col, n):
+        self.log.append(("prepare_start", time.perf_counter()))
+        time.sleep(self.prepare_delay)
+        out = super().prepare(rp, col, n)
+        self.log.append(("prepare_end", time.perf_counter()))
+        return out
+
+    def count_batch(self, hs, ks):
+        self.log.append(("batch_start", time.perf_counter()))
+        return super().count_batch(hs, ks)
+
+    def when(self, what):
+        return [t for w, t in self.log if w == what]
+
+
+@pytest.mark.parametrize("yield_ms,expect", [(0, "after"), (0xFFFFFFFF, "during"), (50, "during")])
+def test_count_batches_wait_for_uploads_in_flight(yield_ms, expect):
+    """Short work first: a count batch waits while an upload is being prepared, at most
+    yield_ms (0 = the default, 1000 ms; KC_SERVER_NO_YIELD = it never waits)."""
+    be = RecordingBackend(prepare_delay=0.4)
+    srv = _server(be, hbm_budget_bytes=1 << 30, yield_ms=yield_ms)
+    base = G.gnp(30, 0.3, seed=1)
+    srv.register("base", *_csr(base))
+    be.log.clear()  # registration prepares too
+    up = G.gnp(25, 0.4, seed=2)
+    fu = srv.submit(_req("upload", "u", csr=_csr(up)))
+    time.sleep(0.05)  # the upload is being prepared
+    fc = srv.submit(_req("count", "base", k=3))
+    assert fc.result(timeout=30).count == O.count(base, 3)["count"]
+    assert fu.result(timeout=30).status == "ok"
+    srv.close()
+    (p_end,), (b_start,) = be.when("prepare_end"), be.when("batch_start")
+    if expect == "after":
+        assert b_start >= p_end
+    else:
+        assert b_start < p_end
