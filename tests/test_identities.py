@@ -1,4 +1,4 @@
-"""The counting identities the branch kernels use for dense l = 4 frames, restated in plain
+"""The counting identities the branch kernels use for dense l = 3 and l = 4 frames, restated in plain
 Python and checked against brute force on random small graphs (CPU).
 
 A 4-set of a frame C is a clique iff it spans no edge of the complement H, so by
@@ -128,3 +128,42 @@ def test_k4_identities_on_dense_frames():
         z = [rng.getrandbits(64) | 1 for _ in range(c)]
         assert k4_count(c, adj) == brute(c, adj), trial
         assert k4_weighted(c, adj, z) == brute(c, adj, z), trial
+
+
+def brute3(c, adj, z=None):
+    total = 0
+    for q in itertools.combinations(range(c), 3):
+        if all(adj[a][b] for a, b in itertools.combinations(q, 2)):
+            total += 1 if z is None else z[q[0]] * z[q[1]] * z[q[2]]
+    return total if z is None else total & M64
+
+
+def k3_identities(c, adj, z):
+    """The l = 3 frame count and its key-weighted form through the complement H:
+    #K3 = C(c,3) - |H|(c-2) + sum_x C(dbar_x, 2) - T(H), and
+    e3(z) - sum_{ab in H} z_a z_b (Z - z_a - z_b) + sum_x z_x e2(keys of x's H-neighbours) - T_z(H)."""
+    H = [[a != b and not adj[a][b] for b in range(c)] for a in range(c)]
+    d = [sum(H[x]) for x in range(c)]
+    M = sum(d) // 2
+    tri_h = [(a, b, w) for a, b, w in itertools.combinations(range(c), 3) if H[a][b] and H[a][w] and H[b][w]]
+    count = comb(c, 3) - M * (c - 2) + sum(comb(x, 2) for x in d) - len(tri_h)
+    e = esym(z, 3)
+    Z, e3 = e[1], e[3]
+    w = e3
+    for a, b in itertools.combinations(range(c), 2):
+        if H[a][b]:
+            w -= z[a] * z[b] * (Z - z[a] - z[b])
+    for x in range(c):
+        w += z[x] * esym([z[y] for y in range(c) if H[x][y]], 2)[2]
+    for a, b, t in tri_h:
+        w -= z[a] * z[b] * z[t]
+    return count, w & M64
+
+
+def test_k3_identities_match_brute_force():
+    rng = random.Random(99)
+    for trial in range(250):
+        c = rng.randint(0, 14)
+        adj = random_graph(rng, c, rng.random())
+        z = [rng.getrandbits(64) | 1 for _ in range(c)]
+        assert k3_identities(c, adj, z) == (brute3(c, adj), brute3(c, adj, z)), trial
